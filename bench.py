@@ -1,0 +1,314 @@
+"""Benchmark of the fused entropic-MRT two-phase lattice Boltzmann step.
+
+Workload: D3Q27 drop impact on a thin film, 512x512x256 nodes, FP32 populations
+in one A-A buffer (7.25 GB, far larger than the 129 MB L2, so no flush is
+needed between steps), density ratio ~1000 (T/Tc = 0.59).  One benchmark step is
+one lattice time step (both passes) over the whole domain.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = MLUPS (million lattice updates per second, whole
+job); e2e = the same metric through the C ABI with host buffers (initial fields
+copied in, K steps, density and velocity copied out); roofline = the
+force+collide+stream kernel's algorithmic bytes per launch over its CUDA-event
+duration, against the measured HBM copy bandwidth; cpu_baseline = the FP64
+oracle on a bounded crop of the same workload on the host cores.
+
+--impl reference times the FP64 CPU oracle (the reference implementation of
+the method) on a bounded crop of the same workload; N > 1: rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded crop of the workload
+# ---------------------------------------------------------------------------
+CPU_CROP = (48, 64, 64)   # nz, ny, nx: 196,608 nodes
+CPU_STEPS = 12
+
+
+def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
+    import oracle as O
+    from oracle import thermo
+    from paper_2201_12404_gb300 import workloads as WL
+    rv, rl, _ = thermo.maxwell(wl.T_over_Tc, **WL.PAPER_EOS)
+    nu_l, nu_v = WL.viscosities(wl, rv, rl)
+    bc = [0] * 6
+    if wl.walls_axis >= 0:
+        bc[2 * wl.walls_axis] = bc[2 * wl.walls_axis + 1] = 1
+    nz, ny, nx = crop
+    p = O.make_params(wl.D, nx, ny, nz, T_over_Tc=wl.T_over_Tc, kappa=wl.kappa, nu_liquid=nu_l,
+                      nu_vapour=nu_v, rho_liquid=rl, rho_vapour=rv, bc=bc, **WL.PAPER_EOS)
+    rho, u = WL.initial_fields(wl, rv, rl, crop=crop)
+    f = O.init_equilibrium(p, rho, u)
+    t0 = time.perf_counter()
+    O.run(p, f, steps)
+    dt = time.perf_counter() - t0
+    lups = nx * ny * nz * steps
+    return {"value": lups / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, {steps} steps of a {nx}x{ny}x{nz} crop of the same D3Q27 drop-on-film "
+                      f"workload (same EOS, kappa, viscosities, walls), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2201_12404_gb300 import workloads as WL
+    wl = WL.by_name(args.workload)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up effects worth a full sample; the first timed sample includes none
+    vals = []
+    for _ in range(max(1, args.steps)):
+        vals.append(oracle_sample(wl, steps=1, crop=CPU_CROP))
+    v = float(np.median([x["value"] for x in vals]))
+    cb = dict(vals[0])
+    cb["value"] = v
+    cb["sample"] = (f"FP64 oracle, 1 step of a {CPU_CROP[2]}x{CPU_CROP[1]}x{CPU_CROP[0]} crop per benchmark "
+                    f"step (median of {len(vals)})")
+    line = {"impl": "reference", "metric": "D3Q27 entropic-MRT MLUPS", "value": v, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": wl.name, "oracle_crop": list(CPU_CROP)},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def algorithmic_bytes_k2(wl, pop_bytes, aux_bytes):
+    """Force+collide+stream kernel: each population read once and written once,
+    each auxiliary field of the node read once (halo re-reads are cache hits)."""
+    Q = 27 if wl.D == 3 else 9
+    return wl.N * (2 * Q * pop_bytes + (2 + wl.D) * aux_bytes)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2201_12404_gb300 import lbm
+    from paper_2201_12404_gb300 import workloads as WL
+    lbm.load()
+
+    wl = WL.by_name(args.workload)
+    rv, rl = WL.coexistence(wl)
+    stream = torch.cuda.current_stream()
+    p = WL.params(wl, lbm.LBM_FP32, stream=stream.cuda_stream, rv=rv, rl=rl)
+    rho0, u0 = WL.initial_fields(wl, rv, rl)
+
+    dom = lbm.Domain(p)
+    dom.lbm_init_fields(rho0, u0)
+    dom.lbm_step(args.warmup)
+    dom.lbm_synchronize()
+
+    # ---- timed region: K steps, device-resident state
+    barrier(world)
+    torch.cuda.synchronize()
+    dom.lbm_set_timing(True)
+    launches0 = dom.lbm_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        dom.lbm_step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = dom.lbm_launch_count() - launches0
+    dom.lbm_synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    kms, kcnt = dom.lbm_kernel_times()
+    dom.lbm_set_timing(False)
+    clocks = clk.summary()
+    mlups = wl.N * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+    h_rho, h_u = pin(rho0), [pin(u0[k]) for k in range(wl.D)]
+    o_rho = torch.empty(wl.N, dtype=torch.float64).pin_memory()
+    o_u = [torch.empty(wl.N, dtype=torch.float64).pin_memory() for _ in range(wl.D)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dom.lbm_init_fields_ptr(h_rho.data_ptr(), h_u[0].data_ptr(), h_u[1].data_ptr(),
+                            h_u[2].data_ptr() if wl.D == 3 else None)
+    dom.lbm_step(args.steps)
+    dom.lbm_read_macroscopic_ptr(o_rho.data_ptr(), o_u[0].data_ptr(), o_u[1].data_ptr(),
+                                 o_u[2].data_ptr() if wl.D == 3 else None)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    assert np.isfinite(o_rho.numpy()).all(), "non-finite density after the e2e run"
+    e2e_mlups = wl.N * args.steps * world / e2e_s / 1e6
+    dom.close()
+
+    if rank != 0:
+        return 0
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    k2_ms = kms[1] / max(1, kcnt[1])
+    k1_ms = kms[0] / max(1, kcnt[0])
+    k2_bytes = algorithmic_bytes_k2(wl, 4, 4)
+    achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        t = prof.get("d3q27_fp32_collide_stream")
+        if t and t.get("kernel_rev") == "v1":
+            traffic = t["bytes_per_launch"]
+    except Exception:
+        pass
+    Q = 27
+    line = {
+        "metric": "D3Q27 entropic-MRT MLUPS (fused two-pass step, FP32 A-A)",
+        "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": wl.N, "lattice": "D3Q27", "storage": "fp32 A-A",
+                   "l2": "inputs larger than L2 (7.25 GB populations), no flush",
+                   "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "collide_stream (force + collide + stream)",
+                     "algorithmic_bytes_per_launch": k2_bytes,
+                     "kernel_ms": k2_ms},
+        "step_roofline": {"bytes_per_lup_floor": 2 * Q * 4,
+                          "frac_of_floor": mlups / world * 1e6 * 2 * Q * 4 / (hbm * 1e9),
+                          "moments_eos_ms": k1_ms, "collide_stream_ms": k2_ms},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS",
+                "h2d_bytes_per_step": (1 + wl.D) * wl.N * 8 / args.steps,
+                "d2h_bytes_per_step": (1 + wl.D) * wl.N * 8 / args.steps,
+                "what": "lbm_init_fields from pinned host arrays + K steps + lbm_read_macroscopic to pinned host"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(wl)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="drop3d", help="drop3d (default, 512x512x256) or drop3d-small "
+                    "(256x256x128, the profiling case)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * lbm.h — C ABI of the GB300 entropic multi-relaxation-time two-phase lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * The method is that of Hosseini, Dorschner & Karlin, "Entropic
+ * multi-relaxation-time lattice Boltzmann model for large density ratio
+ * two-phase flows" (arXiv:2201.12404).  One call of lbm_step advances the
+ * populations f_i of a D2Q9 or D3Q27 lattice by whole time steps of Eq. (LBGK):
+ *
+ *   f_i(r + c_i dt, t + dt) = (1 - w/2) f_i + (w/2) f_i^mirr + (f_i^* - f_i^eq)
+ *
+ * with the product-form equilibria of Sec. 2.2 (Eqs. LBMeq, LBMstar), the
+ * Peng-Robinson pressure of Sec. 3.1 (Eq. PREoS) entering through the
+ * pseudo-potential force of Sec. 2.3 (Eq. Kforce_final), the diagonal
+ * correction Phi (Eq. correction), and the entropic mirror state of Sec. 2.4
+ * (k/s/h split in the central Hermite basis of Appendix A, gamma from the
+ * entropic scalar products).
+ *
+ * Conventions shared by every call:
+ *  - Lattice units: dt = dr = 1, cs^2 = 1/3, P0 = rho cs^2 (Sec. 2.3).
+ *  - Host field arrays are float64, node index x + nx*(y + ny*z), x fastest
+ *    (nz = 1 in 2-D).  The caller owns every host buffer; the library copies.
+ *  - Populations are exchanged in "canonical" order: float64 array of Q*N
+ *    values, element [i*N + node], velocity index i = (cx+1) + 3(cy+1) +
+ *    9(cz+1), holding the post-streaming, pre-collision state.  The opposite
+ *    direction of i is Q-1-i.
+ *  - The library owns all device memory of a domain (allocated in
+ *    lbm_create_domain, freed in lbm_destroy).
+ *  - Every call that launches GPU work enqueues it on the domain's stream and
+ *    returns without waiting, except those documented as synchronising.
+ *  - Handles are not thread-safe: use one handle per host thread or lock.
+ *  - After an error other than LBM_ERR_INVALID_ARG the handle refuses further
+ *    work with LBM_ERR_STATE until destroyed; lbm_last_error() says why.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain* lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID_ARG = 1, /* bad argument; the handle stays usable */
+  LBM_ERR_OOM = 2,         /* device allocation failed */
+  LBM_ERR_CUDA = 3,        /* a CUDA call failed */
+  LBM_ERR_UNSTABLE = 4,    /* a non-finite or non-positive density appeared */
+  LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  LBM_ERR_STATE = 6        /* the handle is poisoned by an earlier error */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q27 = 1 } lbm_lattice;
+
+/* Storage and arithmetic of the populations.
+ * LBM_FP64: stored and computed in float64 (the GPU reference path).
+ * LBM_FP32: stored and computed in float32; float64 only in the Peng-Robinson
+ *           pressure inside the interface band and in the gamma ratio.
+ * LBM_FP16DEV: stored as float16 deviations f_i/(w_i rho_w) - 1, rho_w the
+ *           density of the node that wrote the slot; computed in float32.
+ *           (Not built yet: lbm_create_domain returns LBM_ERR_INVALID_ARG.) */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2 } lbm_precision;
+
+/* Boundary of each face (-x,+x,-y,+y,-z,+z).  Periodic needs both faces of an
+ * axis periodic.  Bounce-back is half-way: the wall sits half a node outside
+ * the first and last node, populations reverse there, and the auxiliary
+ * density/pseudo-potential fields are mirrored across it. */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 } lbm_bc;
+
+/* LBM_GAMMA_ENTROPIC: gamma per node from Sec. 2.4.
+ * LBM_GAMMA_FIXED: gamma = gamma_value everywhere (2 reproduces LBGK; 2/omega
+ * relaxes the higher-order moments fully onto f*). */
+typedef enum { LBM_GAMMA_ENTROPIC = 0, LBM_GAMMA_FIXED = 1 } lbm_gamma_mode;
+
+typedef struct {
+  int32_t lattice;     /* lbm_lattice */
+  int32_t precision;   /* lbm_precision */
+  int32_t nx, ny, nz;  /* nodes per axis, each >= 5; nz must be 1 for D2Q9 */
+  /* Peng-Robinson EOS, Sec. 3.1: a, b, gas constant R, reduced temperature
+   * T/Tc and acentric factor w'.  Tc = 0.0778 a/(0.45724 b R). */
+  double a, b, R, T_over_Tc, acentric;
+  double kappa;        /* capillary coefficient kappa~ = kappa dr^2 of Eq. (Kforce_final), >= 0 */
+  /* Kinematic viscosity: nu(rho) = nu_vapour + phi (nu_liquid - nu_vapour),
+   * phi = clamp((rho - rho_vapour)/(rho_liquid - rho_vapour), 0, 1); local
+   * omega = 1/(3 nu + 1/2) (Sec. 2.1 with P0 = rho cs^2).  Equal viscosities
+   * give a uniform omega.  rho_liquid > rho_vapour > 0 is required. */
+  double nu_liquid, nu_vapour, rho_liquid, rho_vapour;
+  double body_force[3]; /* uniform acceleration g: adds rho*g to the force */
+  int32_t bc[6];        /* lbm_bc per face -x,+x,-y,+y,-z,+z (z faces ignored in 2-D) */
+  int32_t gamma_mode;   /* lbm_gamma_mode */
+  double gamma_value;   /* used when gamma_mode == LBM_GAMMA_FIXED */
+  /* FP32 path only: 0 = Peng-Robinson pressure in float32 everywhere,
+   * 1 = in float64 where rho lies inside the interface band (default),
+   * 2 = float64 everywhere. */
+  int32_t eos_fp64;
+  void* stream;         /* cudaStream_t to run on; NULL = a stream the library creates */
+} lbm_params;
+
+/* Fill p with defaults: D2Q9 FP32 64x64, the paper's EOS constants
+ * (a = 0.003, b = 0.095, R = 1, w' = 0.344, Sec. 3.1), T/Tc = 0.8, kappa = 0,
+ * nu = 0.1, rho_liquid = 1, rho_vapour = 0.5, periodic, entropic gamma,
+ * eos_fp64 = 1, NULL stream. */
+lbm_status lbm_default_params(lbm_params* p);
+
+/* Validate p, allocate the domain's device memory and create its handle.
+ * *out receives the handle (NULL on failure).  Errors: INVALID_ARG (message via
+ * lbm_last_error(NULL)), OOM, CUDA. */
+lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out);
+
+/* f := f^eq(rho, u) (Eq. LBMeq) at every node from host arrays of N values
+ * each (uz is NULL in 2-D).  u is the bare velocity sum_i c_i f_i / rho.
+ * Resets the step counter and the streaming parity.  Synchronising. */
+lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, const double* uy,
+                           const double* uz);
+
+/* Advance nsteps >= 0 time steps (asynchronous).  An instability detected by
+ * an earlier call surfaces here or in any later synchronising call as
+ * LBM_ERR_UNSTABLE. */
+lbm_status lbm_step(lbm_handle h, int64_t nsteps);
+
+/* Wait for the domain's stream; report LBM_ERR_UNSTABLE if a non-finite or
+ * non-positive density has appeared.  Synchronising. */
+lbm_status lbm_synchronize(lbm_handle h);
+
+/* Density and velocity of the current state into host arrays of N values each
+ * (uz ignored/NULL in 2-D).  The velocity is the exact-difference-method
+ * velocity u + F dt/(2 rho).  Synchronising. */
+lbm_status lbm_read_macroscopic(lbm_handle h, double* rho, double* ux, double* uy, double* uz);
+
+/* Release the domain.  NULL-safe. */
+lbm_status lbm_destroy(lbm_handle h);
+
+/* Canonical populations (see conventions) as float64, count = Q*N.
+ * Synchronising. */
+lbm_status lbm_read_populations(lbm_handle h, double* host, size_t count);
+
+/* Replace the state with canonical populations (float64, count = Q*N; rounded
+ * to the storage precision).  Resets the streaming parity.  Synchronising. */
+lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count);
+
+/* Totals of the current state: mass sum rho, momentum sum_i c_i f_i (3 values,
+ * bare), max |u| of the bare velocity.  gamma_field (nullable) receives, per
+ * node (N values), the gamma of the last step run while gamma recording was on
+ * (lbm_record_gamma), zeros otherwise.  Deterministic.  Synchronising. */
+lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* max_u,
+                         double* gamma_field);
+
+/* Turn per-node gamma recording on (enable != 0) or off for later lbm_step
+ * calls.  Recording adds a float32 store per node and step (the 2/(omega gamma)
+ * field of Sec. 3.3 is derived from it). */
+lbm_status lbm_record_gamma(lbm_handle h, int enable);
+
+/* Number of nodes where the f*_i <= 0 guard set gamma = 2, summed over all
+ * steps since creation.  Synchronising. */
+lbm_status lbm_guard_count(lbm_handle h, uint64_t* count);
+
+/* Device bytes lbm_create_domain would allocate for p (0 if p is invalid). */
+size_t lbm_footprint_bytes(const lbm_params* p);
+
+/* Maxwell equal-area coexistence of the Peng-Robinson EOS (Sec. 3.1.1,
+ * Eq. Maxwell_equal_area) for the EOS fields of p: densities of the vapour and
+ * liquid and the saturation pressure.  Host-only. */
+lbm_status lbm_coexistence(const lbm_params* p, double* rho_vapour, double* rho_liquid, double* p_sat);
+
+/* Kernel timing on the domain's stream with CUDA events.  When enabled, every
+ * launch made by lbm_step is bracketed by events; lbm_kernel_times then
+ * synchronises and returns, per kernel kind, the summed milliseconds and the
+ * launch count: ms[0]/count[0] moments+EOS kernel, ms[1]/count[1]
+ * force+collide+stream kernel.  Enabling resets the sums. */
+lbm_status lbm_set_timing(lbm_handle h, int enable);
+lbm_status lbm_kernel_times(lbm_handle h, double ms[2], int64_t count[2]);
+
+/* Kernels this handle has launched since creation (all kinds). */
+int64_t lbm_launch_count(lbm_handle h);
+
+/* Message of the last error on h, or of the last failed lbm_create_domain /
+ * lbm_coexistence on this thread when h is NULL.  Never NULL. */
+const char* lbm_last_error(lbm_handle h);
+
+/* Library build string (lattices, precisions, target architecture). */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -111,6 +111,7 @@ def lib():
                 "orc_step": (ctypes.c_long, [P, _dp, _dp, ctypes.c_void_p]),
                 "orc_run": (ctypes.c_long, [P, _dp, ctypes.c_long]),
                 "orc_totals": (None, [P, _dp, ctypes.POINTER(ctypes.c_double), _dp]),
+                "orc_num_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -290,3 +291,8 @@ def totals(p: Params, f):
     j = np.zeros(3)
     lib().orc_totals(ctypes.byref(p), _f64(f), ctypes.byref(m), j)
     return m.value, j
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's step uses."""
+    return int(lib().orc_num_threads())

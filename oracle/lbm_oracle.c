@@ -33,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MAXQ 27
 
@@ -550,4 +553,13 @@ void orc_totals(const orc_params* p, const double* f, double* mass, double* mom 
     }
   *mass = m;
   for (int al = 0; al < 3; ++al) mom[al] = j[al];
+}
+
+/* Threads the OpenMP loops of orc_step use (1 without OpenMP). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

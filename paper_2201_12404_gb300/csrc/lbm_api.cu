@@ -1,0 +1,570 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation,
+// device memory, the step loop, field I/O, diagnostics and timing.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_ops.h"
+
+using lbm::DevDomain;
+using lbm::Ops;
+
+struct lbm_domain {
+  lbm_params p{};
+  const Ops* ops = nullptr;
+  DevDomain dev{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int parity = 0;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  bool poisoned = false;
+  std::string err;
+  // error flags: device word, pinned host mirror, event marking the mirror's copy
+  unsigned int* h_flags = nullptr;
+  cudaEvent_t flags_ev = nullptr;
+  bool flags_pending = false;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Mark { int kind; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  double ms[2] = {0, 0};
+  int64_t cnt[2] = {0, 0};
+  bool record_gamma = false;
+};
+
+static thread_local std::string g_create_error = "no error";
+
+namespace {
+
+const char* kVersion = "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP32, A-A streaming, sm_103a";
+
+bool is_wall(int v) { return v == LBM_BC_BOUNCEBACK; }
+
+struct EosCoeffs { double RT, b, aalpha, Tc; };
+
+EosCoeffs eos_coeffs(const lbm_params& p) {
+  EosCoeffs e;
+  e.Tc = 0.0778 * p.a / (0.45724 * p.b * p.R);
+  const double T = p.T_over_Tc * e.Tc;
+  const double m = 0.37464 + 1.54226 * p.acentric - 0.26992 * p.acentric * p.acentric;
+  const double s = 1.0 + m * (1.0 - std::sqrt(p.T_over_Tc));
+  e.RT = p.R * T;
+  e.b = p.b;
+  e.aalpha = p.a * s * s;
+  return e;
+}
+
+double pr_p(const EosCoeffs& e, double rho) {
+  return rho * e.RT / (1.0 - e.b * rho) - e.aalpha * rho * rho / (1.0 + 2.0 * e.b * rho - e.b * e.b * rho * rho);
+}
+
+std::string validate(const lbm_params* p) {
+  if (!p) return "params is NULL";
+  if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q27) return "lattice must be LBM_D2Q9 or LBM_D3Q27";
+  if (p->precision == LBM_FP16DEV) return "LBM_FP16DEV storage is not available in this build";
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return "precision must be LBM_FP64 or LBM_FP32";
+  const bool d3 = p->lattice == LBM_D3Q27;
+  if (p->nx < 5 || p->ny < 5) return "nx and ny must be >= 5 (stencil radius 2)";
+  if (d3 && p->nz < 5) return "nz must be >= 5 for D3Q27";
+  if (!d3 && p->nz != 1) return "nz must be 1 for D2Q9";
+  if ((double)p->nx * p->ny * p->nz > 4.0e9) return "domain larger than 4e9 nodes";
+  if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0)) return "EOS a, b, R must be > 0";
+  if (!(p->T_over_Tc > 0) || !(p->T_over_Tc < 1.5)) return "T_over_Tc must lie in (0, 1.5)";
+  if (!std::isfinite(p->acentric)) return "acentric factor must be finite";
+  if (!(p->kappa >= 0) || !std::isfinite(p->kappa)) return "kappa must be >= 0";
+  if (!(p->nu_liquid > 0) || !(p->nu_vapour > 0)) return "viscosities must be > 0";
+  if (!(p->rho_vapour > 0) || !(p->rho_liquid > p->rho_vapour)) return "need rho_liquid > rho_vapour > 0";
+  for (int k = 0; k < 3; ++k) if (!std::isfinite(p->body_force[k])) return "body_force must be finite";
+  for (int k = 0; k < 6; ++k)
+    if (p->bc[k] != LBM_BC_PERIODIC && p->bc[k] != LBM_BC_BOUNCEBACK) return "bc entries must be 0 or 1";
+  for (int a = 0; a < (d3 ? 3 : 2); ++a)
+    if ((p->bc[2 * a] == LBM_BC_PERIODIC) != (p->bc[2 * a + 1] == LBM_BC_PERIODIC))
+      return "periodic faces must come in pairs";
+  if (!d3 && (p->body_force[2] != 0.0)) return "body_force[2] must be 0 in 2-D";
+  if (p->gamma_mode != LBM_GAMMA_ENTROPIC && p->gamma_mode != LBM_GAMMA_FIXED) return "gamma_mode must be 0 or 1";
+  if (p->gamma_mode == LBM_GAMMA_FIXED && !std::isfinite(p->gamma_value)) return "gamma_value must be finite";
+  if (p->eos_fp64 < 0 || p->eos_fp64 > 2) return "eos_fp64 must be 0, 1 or 2";
+  return "";
+}
+
+struct Sizes { int D, Q; long long N, PN; int px, py, pz; size_t f_bytes, aux_bytes, gamma_bytes; };
+
+Sizes sizes_of(const lbm_params& p, const Ops* ops) {
+  Sizes s;
+  s.D = p.lattice == LBM_D3Q27 ? 3 : 2;
+  s.Q = s.D == 3 ? 27 : 9;
+  s.N = (long long)p.nx * p.ny * (s.D == 3 ? p.nz : 1);
+  s.px = p.nx + 4;
+  s.py = p.ny + 4;
+  s.pz = s.D == 3 ? p.nz + 4 : 1;
+  s.PN = (long long)s.px * s.py * s.pz;
+  s.f_bytes = (size_t)s.Q * s.N * ops->pop_bytes;
+  s.aux_bytes = (size_t)(2 + s.D) * s.PN * ops->aux_bytes;
+  s.gamma_bytes = (size_t)s.N * sizeof(float);
+  return s;
+}
+
+const Ops* ops_for(const lbm_params& p) {
+  if (p.lattice == LBM_D2Q9) return p.precision == LBM_FP64 ? &lbm::ops_d2q9_fp64 : &lbm::ops_d2q9_fp32;
+  return p.precision == LBM_FP64 ? &lbm::ops_d3q27_fp64 : &lbm::ops_d3q27_fp32;
+}
+
+lbm_status fail(lbm_domain* h, lbm_status st, const std::string& msg) {
+  h->err = msg;
+  if (st != LBM_ERR_INVALID_ARG) h->poisoned = true;
+  return st;
+}
+
+lbm_status cuda_fail(lbm_domain* h, cudaError_t e, const char* where) {
+  return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(h, call)                                     \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
+  } while (0)
+
+#define LBM_LIVE(h)                                                               \
+  do {                                                                            \
+    if (!(h)) return LBM_ERR_INVALID_ARG;                                         \
+    if ((h)->poisoned) return LBM_ERR_STATE;                                      \
+  } while (0)
+
+cudaEvent_t take_event(lbm_domain* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold finished timing marks into the sums (synchronous).
+lbm_status drain_marks(lbm_domain* h) {
+  for (auto& m : h->marks) {
+    float t = 0;
+    LBM_CUDA(h, cudaEventSynchronize(m.b));
+    LBM_CUDA(h, cudaEventElapsedTime(&t, m.a, m.b));
+    h->ms[m.kind] += t;
+    h->cnt[m.kind] += 1;
+    h->ev_pool.push_back(m.a);
+    h->ev_pool.push_back(m.b);
+  }
+  h->marks.clear();
+  return LBM_OK;
+}
+
+// Check the error flags copied by earlier steps without waiting for the GPU.
+lbm_status poll_flags(lbm_domain* h, bool wait) {
+  if (!h->flags_pending) return LBM_OK;
+  if (wait) {
+    LBM_CUDA(h, cudaEventSynchronize(h->flags_ev));
+  } else {
+    cudaError_t q = cudaEventQuery(h->flags_ev);
+    if (q == cudaErrorNotReady) return LBM_OK;
+    if (q != cudaSuccess) return cuda_fail(h, q, "cudaEventQuery");
+  }
+  h->flags_pending = false;
+  if (*h->h_flags & 1u) return fail(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density in the domain");
+  return LBM_OK;
+}
+
+lbm_status enqueue_flag_copy(lbm_domain* h) {
+  LBM_CUDA(h, cudaMemcpyAsync(h->h_flags, h->dev.flags, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaEventRecord(h->flags_ev, h->stream));
+  h->flags_pending = true;
+  return LBM_OK;
+}
+
+lbm_status launch_k(lbm_domain* h, int kind) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->timing) {
+    a = take_event(h);
+    b = take_event(h);
+    LBM_CUDA(h, cudaEventRecord(a, h->stream));
+  }
+  if (kind == 0) h->ops->moments_eos(h->dev, h->parity, h->stream);
+  else h->ops->collide_stream(h->dev, h->parity, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  if (h->timing) {
+    LBM_CUDA(h, cudaEventRecord(b, h->stream));
+    h->marks.push_back({kind, a, b});
+  }
+  return LBM_OK;
+}
+
+// Run pass 1 for the current state (refreshes the auxiliary fields).
+lbm_status refresh_aux(lbm_domain* h) {
+  h->ops->moments_eos(h->dev, h->parity, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  return LBM_OK;
+}
+
+// ---- Maxwell construction (host) ----
+// In density: int_{rv}^{rl} (Psat - P)/rho^2 drho = [ -Psat/rho - G(rho) ]_{rv}^{rl}, with the
+// antiderivative of P/rho^2 for Peng-Robinson
+//   G(rho) = RT ln(rho/(1 - b rho)) + aalpha/(2 sqrt2 b) ln|(rho - r1)/(rho - r2)|,
+// r1,2 = (1 +- sqrt2)/b the roots of 1 + 2 b rho - b^2 rho^2.
+double antideriv(const EosCoeffs& e, double rho) {
+  const double s2 = std::sqrt(2.0);
+  const double r1 = (1.0 + s2) / e.b, r2 = (1.0 - s2) / e.b;
+  return e.RT * std::log(rho / (1.0 - e.b * rho)) + e.aalpha / (2.0 * s2 * e.b) * std::log(std::fabs((rho - r1) / (rho - r2)));
+}
+
+double dpdrho(const EosCoeffs& e, double rho) {
+  const double h = 1e-7 * std::max(rho, 1e-6);
+  return (pr_p(e, rho + h) - pr_p(e, rho - h)) / (2 * h);
+}
+
+// root of P(rho) = target on [lo, hi] where P - target changes sign
+double bisect_p(const EosCoeffs& e, double target, double lo, double hi) {
+  double flo = pr_p(e, lo) - target;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double fm = pr_p(e, mid) - target;
+    if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+    if (hi - lo <= 1e-15 * hi) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_version(void) { return kVersion; }
+
+lbm_status lbm_default_params(lbm_params* p) {
+  if (!p) return LBM_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->lattice = LBM_D2Q9;
+  p->precision = LBM_FP32;
+  p->nx = 64; p->ny = 64; p->nz = 1;
+  p->a = 0.003; p->b = 0.095; p->R = 1.0; p->T_over_Tc = 0.8; p->acentric = 0.344;
+  p->kappa = 0.0;
+  p->nu_liquid = 0.1; p->nu_vapour = 0.1; p->rho_liquid = 1.0; p->rho_vapour = 0.5;
+  p->gamma_mode = LBM_GAMMA_ENTROPIC; p->gamma_value = 2.0;
+  p->eos_fp64 = 1;
+  p->stream = nullptr;
+  return LBM_OK;
+}
+
+size_t lbm_footprint_bytes(const lbm_params* p) {
+  if (!validate(p).empty()) return 0;
+  Sizes s = sizes_of(*p, ops_for(*p));
+  return s.f_bytes + s.aux_bytes + sizeof(unsigned int) + sizeof(unsigned long long);
+}
+
+lbm_status lbm_coexistence(const lbm_params* p, double* rho_vapour, double* rho_liquid, double* p_sat) {
+  if (!p || !rho_vapour || !rho_liquid) { g_create_error = "NULL argument"; return LBM_ERR_INVALID_ARG; }
+  if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0) || !(p->T_over_Tc > 0) || !(p->T_over_Tc < 1)) {
+    g_create_error = "coexistence needs a, b, R > 0 and 0 < T/Tc < 1";
+    return LBM_ERR_INVALID_ARG;
+  }
+  const EosCoeffs e = eos_coeffs(*p);
+  // spinodals: the local maximum (vapour side) and minimum (liquid side) of P(rho) on (0, 1/b)
+  const double rmax = 1.0 / e.b;
+  const int M = 200000;
+  double r_spv = -1, r_spl = -1;
+  double prev = dpdrho(e, rmax * 1e-6);
+  for (int k = 1; k <= M; ++k) {
+    const double r = rmax * (1e-6 + (0.999 - 1e-6) * k / M);
+    const double d = dpdrho(e, r);
+    if (r_spv < 0 && prev > 0 && d <= 0) r_spv = r;
+    else if (r_spv > 0 && prev < 0 && d >= 0) { r_spl = r; break; }
+    prev = d;
+  }
+  if (r_spv < 0 || r_spl < 0) { g_create_error = "no two-phase region at this temperature"; return LBM_ERR_INVALID_ARG; }
+  const double p_hi = pr_p(e, r_spv), p_lo = std::max(pr_p(e, r_spl), 1e-300);
+  double rv = 0, rl = 0;
+  auto area = [&](double Ps) {
+    rv = bisect_p(e, Ps, 0.0, r_spv);
+    rl = bisect_p(e, Ps, r_spl, rmax * 0.999999);
+    return (-Ps / rl - antideriv(e, rl)) - (-Ps / rv - antideriv(e, rv));
+  };
+  double lo = p_lo + 1e-12 * (p_hi - p_lo), hi = p_hi - 1e-12 * (p_hi - p_lo);
+  double flo = area(lo);
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double fm = area(mid);
+    if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+    if (hi - lo <= 1e-16 * hi) break;
+  }
+  const double Ps = 0.5 * (lo + hi);
+  area(Ps);
+  *rho_vapour = rv;
+  *rho_liquid = rl;
+  if (p_sat) *p_sat = Ps;
+  return LBM_OK;
+}
+
+lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
+  if (!out) { g_create_error = "out is NULL"; return LBM_ERR_INVALID_ARG; }
+  *out = nullptr;
+  const std::string why = validate(p);
+  if (!why.empty()) { g_create_error = why; return LBM_ERR_INVALID_ARG; }
+
+  lbm_domain* h = new lbm_domain();
+  h->p = *p;
+  h->ops = ops_for(*p);
+  const Sizes s = sizes_of(*p, h->ops);
+  DevDomain& d = h->dev;
+  d.N = s.N; d.PN = s.PN;
+  d.nx = p->nx; d.ny = p->ny; d.nz = s.D == 3 ? p->nz : 1;
+  d.px = s.px; d.py = s.py; d.pz = s.pz;
+  for (int a = 0; a < 3; ++a) {
+    const bool active = a < s.D;
+    d.wall_lo[a] = active && is_wall(p->bc[2 * a]);
+    d.wall_hi[a] = active && is_wall(p->bc[2 * a + 1]);
+  }
+  d.kappa = p->kappa;
+  for (int a = 0; a < 3; ++a) d.g[a] = a < s.D ? p->body_force[a] : 0.0;
+  d.nu_v = p->nu_vapour;
+  d.dnu = p->nu_liquid - p->nu_vapour;
+  d.rho_v = p->rho_vapour;
+  d.inv_drho = 1.0 / (p->rho_liquid - p->rho_vapour);
+  const EosCoeffs e = eos_coeffs(*p);
+  d.RT = e.RT; d.b = e.b; d.aalpha = e.aalpha;
+  d.gamma_mode = p->gamma_mode;
+  d.gamma_value = p->gamma_value;
+  d.eos_fp64 = p->eos_fp64;
+  // interface band: densities between the phases, 1% of the density jump inside each bulk value
+  const double span = p->rho_liquid - p->rho_vapour;
+  d.band_lo = p->rho_vapour + 0.01 * span;
+  d.band_hi = p->rho_liquid - 0.01 * span;
+
+  auto bail = [&](cudaError_t err, const char* where) {
+    g_create_error = std::string(where) + ": " + cudaGetErrorString(err);
+    lbm_status st = err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+    lbm_destroy(h);
+    return st;
+  };
+  cudaError_t err;
+  if (p->stream) {
+    h->stream = (cudaStream_t)p->stream;
+  } else {
+    if ((err = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(err, "cudaStreamCreate");
+    h->own_stream = true;
+  }
+  if ((err = cudaMalloc(&d.f, s.f_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(populations)");
+  if ((err = cudaMalloc(&d.aux, s.aux_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(aux)");
+  if ((err = cudaMalloc(&d.flags, sizeof(unsigned int) + sizeof(unsigned long long) * 2)) != cudaSuccess)
+    return bail(err, "cudaMalloc(flags)");
+  d.guards = (unsigned long long*)((char*)d.flags + sizeof(unsigned long long));
+  if ((err = cudaMemsetAsync(d.flags, 0, sizeof(unsigned int) + sizeof(unsigned long long) * 2, h->stream)) != cudaSuccess)
+    return bail(err, "cudaMemset(flags)");
+  if ((err = cudaMemsetAsync(d.aux, 0, s.aux_bytes, h->stream)) != cudaSuccess) return bail(err, "cudaMemset(aux)");
+  if ((err = cudaMallocHost(&h->h_flags, sizeof(unsigned int))) != cudaSuccess) return bail(err, "cudaMallocHost");
+  *h->h_flags = 0;
+  if ((err = cudaEventCreateWithFlags(&h->flags_ev, cudaEventDisableTiming)) != cudaSuccess) return bail(err, "cudaEventCreate");
+  if ((err = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(err, "cudaStreamSynchronize");
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_handle h) {
+  if (!h) return LBM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->dev.f) cudaFree(h->dev.f);
+  if (h->dev.aux) cudaFree(h->dev.aux);
+  if (h->dev.flags) cudaFree(h->dev.flags);
+  if (h->dev.gamma_out) cudaFree(h->dev.gamma_out);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  if (h->flags_ev) cudaEventDestroy(h->flags_ev);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, const double* uy, const double* uz) {
+  LBM_LIVE(h);
+  const int D = h->ops->D;
+  if (!rho || !ux || !uy || (D == 3 && !uz)) return fail(h, LBM_ERR_INVALID_ARG, "NULL field array");
+  const size_t nb = (size_t)h->dev.N * sizeof(double);
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, nb * (1 + D), h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(buf, rho, nb, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(buf + h->dev.N, ux, nb, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(buf + 2 * h->dev.N, uy, nb, cudaMemcpyHostToDevice, h->stream));
+  if (D == 3) LBM_CUDA(h, cudaMemcpyAsync(buf + 3 * h->dev.N, uz, nb, cudaMemcpyHostToDevice, h->stream));
+  h->ops->init_equilibrium(h->dev, buf, buf + h->dev.N, buf + 2 * h->dev.N, D == 3 ? buf + 3 * h->dev.N : nullptr, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->parity = 0;
+  h->steps = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
+  LBM_LIVE(h);
+  if (nsteps < 0) return fail(h, LBM_ERR_INVALID_ARG, "nsteps < 0");
+  lbm_status st = poll_flags(h, false);
+  if (st != LBM_OK) return st;
+  if (h->record_gamma && !h->dev.gamma_out) {
+    LBM_CUDA(h, cudaMalloc(&h->dev.gamma_out, (size_t)h->dev.N * sizeof(float)));
+    LBM_CUDA(h, cudaMemsetAsync(h->dev.gamma_out, 0, (size_t)h->dev.N * sizeof(float), h->stream));
+  }
+  DevDomain saved = h->dev;
+  if (!h->record_gamma) h->dev.gamma_out = nullptr;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if ((st = launch_k(h, 0)) != LBM_OK) break;
+    if ((st = launch_k(h, 1)) != LBM_OK) break;
+    h->parity ^= 1;
+    h->steps += 1;
+  }
+  h->dev.gamma_out = saved.gamma_out;
+  if (st != LBM_OK) return st;
+  if (nsteps > 0 && !h->flags_pending) return enqueue_flag_copy(h);
+  return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_handle h) {
+  LBM_LIVE(h);
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  lbm_status st = poll_flags(h, true);
+  if (st != LBM_OK) return st;
+  // flags of the most recent steps
+  LBM_CUDA(h, cudaMemcpy(h->h_flags, h->dev.flags, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+  if (*h->h_flags & 1u) return fail(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density in the domain");
+  return LBM_OK;
+}
+
+lbm_status lbm_read_macroscopic(lbm_handle h, double* rho, double* ux, double* uy, double* uz) {
+  LBM_LIVE(h);
+  const int D = h->ops->D;
+  if (!rho || !ux || !uy || (D == 3 && !uz)) return fail(h, LBM_ERR_INVALID_ARG, "NULL field array");
+  lbm_status st = refresh_aux(h);
+  if (st != LBM_OK) return st;
+  const size_t nb = (size_t)h->dev.N * sizeof(double);
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, nb * (1 + D), h->stream));
+  h->ops->macroscopic(h->dev, h->parity, buf, buf + h->dev.N, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  LBM_CUDA(h, cudaMemcpyAsync(rho, buf, nb, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(ux, buf + h->dev.N, nb, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(uy, buf + 2 * h->dev.N, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (D == 3) LBM_CUDA(h, cudaMemcpyAsync(uz, buf + 3 * h->dev.N, nb, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  return lbm_synchronize(h);
+}
+
+lbm_status lbm_read_populations(lbm_handle h, double* host, size_t count) {
+  LBM_LIVE(h);
+  const size_t want = (size_t)h->ops->Q * h->dev.N;
+  if (!host || count != want) return fail(h, LBM_ERR_INVALID_ARG, "populations buffer must hold Q*N doubles");
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, want * sizeof(double), h->stream));
+  h->ops->canonical_read(h->dev, h->parity, buf, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  LBM_CUDA(h, cudaMemcpyAsync(host, buf, want * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count) {
+  LBM_LIVE(h);
+  const size_t want = (size_t)h->ops->Q * h->dev.N;
+  if (!host || count != want) return fail(h, LBM_ERR_INVALID_ARG, "populations buffer must hold Q*N doubles");
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, want * sizeof(double), h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(buf, host, want * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->ops->canonical_write(h->dev, buf, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->parity = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* max_u, double* gamma_field) {
+  LBM_LIVE(h);
+  const long long nblk = (h->dev.N + 255) / 256;
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)(nblk * 5 + 5) * sizeof(double), h->stream));
+  int nb = h->ops->diag_partial(h->dev, h->parity, buf, h->stream);
+  lbm::launch_diag_final(buf, nb, buf + nblk * 5, h->stream);
+  h->launches += 2;
+  LBM_CUDA(h, cudaGetLastError());
+  double out[5];
+  LBM_CUDA(h, cudaMemcpyAsync(out, buf + nblk * 5, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (mass) *mass = out[0];
+  if (momentum3) { momentum3[0] = out[1]; momentum3[1] = out[2]; momentum3[2] = out[3]; }
+  if (max_u) *max_u = out[4];
+  if (gamma_field) {
+    if (h->dev.gamma_out) {
+      std::vector<float> g((size_t)h->dev.N);
+      LBM_CUDA(h, cudaMemcpy(g.data(), h->dev.gamma_out, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+      for (size_t k = 0; k < g.size(); ++k) gamma_field[k] = g[k];
+    } else {
+      for (long long k = 0; k < h->dev.N; ++k) gamma_field[k] = 0.0;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_record_gamma(lbm_handle h, int enable) {
+  LBM_LIVE(h);
+  h->record_gamma = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_guard_count(lbm_handle h, uint64_t* count) {
+  LBM_LIVE(h);
+  if (!count) return fail(h, LBM_ERR_INVALID_ARG, "count is NULL");
+  unsigned long long c = 0;
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  LBM_CUDA(h, cudaMemcpy(&c, h->dev.guards, sizeof(c), cudaMemcpyDeviceToHost));
+  *count = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_timing(lbm_handle h, int enable) {
+  LBM_LIVE(h);
+  lbm_status st = drain_marks(h);
+  if (st != LBM_OK) return st;
+  h->timing = enable != 0;
+  h->ms[0] = h->ms[1] = 0;
+  h->cnt[0] = h->cnt[1] = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_times(lbm_handle h, double ms[2], int64_t count[2]) {
+  LBM_LIVE(h);
+  lbm_status st = drain_marks(h);
+  if (st != LBM_OK) return st;
+  if (ms) { ms[0] = h->ms[0]; ms[1] = h->ms[1]; }
+  if (count) { count[0] = h->cnt[0]; count[1] = h->cnt[1]; }
+  return LBM_OK;
+}
+
+int64_t lbm_launch_count(lbm_handle h) { return h ? h->launches : 0; }
+
+const char* lbm_last_error(lbm_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.empty() ? "no error" : h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Device-side building blocks of the entropic MRT two-phase lattice Boltzmann
+// step (Hosseini, Dorschner & Karlin, arXiv:2201.12404) for sm_103a.
+//
+// Data layout in HBM (one domain):
+//   populations  f[i * N + node]          SoA, node = x + nx*(y + ny*z), one A-A buffer
+//   auxiliary    aux[field * PN + pnode]  fields rho, s*psi, q_x, q_y(, q_z); padded by a
+//                                         2-node ghost layer on every axis (2-D: z not padded)
+// The A-A pattern keeps one population buffer: an even step reads and writes the
+// node's own slots (writing direction i into slot Q-1-i), an odd step reads the
+// neighbours' slots and writes back into them, so that after each odd step slot i
+// of node r holds f_i(r) again.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---- lattice: velocities c_i in {-1,0,1}^D, i = (cx+1) + 3(cy+1) + 9(cz+1) (Sec. 2.1) ----
+__host__ __device__ constexpr int cxi(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cyi(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int czi(int i) { return i / 9 - 1; }
+template <int D> __host__ __device__ constexpr int cq(int i, int a) {
+  return a == 0 ? cxi(i) : (a == 1 ? cyi(i) : (D == 3 ? czi(i) : 0));
+}
+template <int D> struct Lattice { static constexpr int Q = D == 2 ? 9 : 27; static constexpr int REST = (Q - 1) / 2; };
+
+// One-dimensional weight Psi_c(0, cs^2): 2/3 at rest, 1/6 moving (Eq. wi).
+__host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+template <int D> __host__ __device__ constexpr double wq(int i) {
+  return w1d(cxi(i)) * w1d(cyi(i)) * (D == 3 ? w1d(czi(i)) : 1.0);
+}
+
+// ---- what a kernel needs to know about a domain (passed by value) ----
+struct DevDomain {
+  void* f;             // populations (storage type)
+  void* aux;           // padded auxiliary fields (float64 in the FP64 path, float32 otherwise)
+  float* gamma_out;    // per-node gamma of the last step, or nullptr
+  unsigned int* flags; // bit 0: non-finite or non-positive density seen
+  unsigned long long* guards; // nodes where f*_i <= 0 forced gamma = 2
+  long long N, PN;     // interior and padded node counts
+  int nx, ny, nz;      // nz = 1 in 2-D
+  int px, py, pz;      // padded extents (pz = 1 in 2-D)
+  int wall_lo[3], wall_hi[3];
+  // physics
+  double kappa, g[3];
+  double nu_v, dnu, rho_v, inv_drho;  // nu(rho) = nu_v + clamp((rho-rho_v)*inv_drho, 0, 1) * dnu
+  double RT, b, aalpha;               // Peng-Robinson: P = rho RT/(1-b rho) - aalpha rho^2/(1+2 b rho-b^2 rho^2)
+  int gamma_mode;
+  double gamma_value;
+  int eos_fp64;
+  double band_lo, band_hi;            // interface band of densities for eos_fp64 == 1
+};
+
+// ---- storage conversion ----
+template <typename S, typename R> __device__ __forceinline__ R ld_pop(const S* p) { return (R)(*p); }
+template <typename S, typename R> __device__ __forceinline__ void st_pop(S* p, R v) { *p = (S)v; }
+
+__device__ __forceinline__ long long node_of(const DevDomain& d, int x, int y, int z) {
+  return (long long)x + (long long)d.nx * ((long long)y + (long long)d.ny * (long long)z);
+}
+template <int D>
+__device__ __forceinline__ long long pnode_of(const DevDomain& d, int x, int y, int z) {
+  return (long long)(x + 2) + (long long)d.px * ((long long)(y + 2) + (long long)d.py * (long long)(D == 3 ? z + 2 : 0));
+}
+
+// Neighbour coordinate along one axis: periodic wrap, or -1 when the link crosses a wall.
+__device__ __forceinline__ int step_axis(int x, int c, int n, int wlo, int whi, bool& wall) {
+  int t = x + c;
+  if (t < 0) { if (wlo) wall = true; else t += n; }
+  else if (t >= n) { if (whi) wall = true; else t -= n; }
+  return t;
+}
+
+// Pre-collision populations of node (x,y,z) for the given A-A parity (0: even
+// step, natural layout; 1: odd step, populations sit reversed at the upstream node).
+template <int D, typename S, typename R>
+__device__ __forceinline__ void gather(const DevDomain& d, int parity, int x, int y, int z, R* f) {
+  constexpr int Q = Lattice<D>::Q;
+  const S* F = (const S*)d.f;
+  const long long n = node_of(d, x, y, z);
+  if (parity == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + (long long)i * d.N + n);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bool wall = false;
+      int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
+      int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
+      int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
+      long long src = wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz);
+      f[i] = ld_pop<S, R>(F + src);
+    }
+  }
+}
+
+// Write post-collision populations: streaming f_i(r + c_i) <- f'_i(r), half-way
+// bounce-back f_{Q-1-i}(r) <- f'_i(r) when r + c_i lies beyond a wall.
+template <int D, typename S, typename R>
+__device__ __forceinline__ void scatter(const DevDomain& d, int parity, int x, int y, int z, const R* fo) {
+  constexpr int Q = Lattice<D>::Q;
+  S* F = (S*)d.f;
+  const long long n = node_of(d, x, y, z);
+  if (parity == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_pop<S, R>(F + (long long)(Q - 1 - i) * d.N + n, fo[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bool wall = false;
+      int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
+      int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
+      int tz = D == 3 ? step_axis(z, czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
+      long long dst = wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz);
+      st_pop<S, R>(F + dst, fo[i]);
+    }
+  }
+}
+
+// rho = sum_i f_i (ascending i), j = sum_i c_i f_i, Pi_ab = sum_i c_ia c_ib f_i.
+// Pi order: xx, yy, zz, xy, xz, yz.
+template <int D, typename R>
+__device__ __forceinline__ void moments(const R* f, R& rho, R* j, R* Pi) {
+  constexpr int Q = Lattice<D>::Q;
+  rho = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) rho += f[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) j[a] = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Pi[k] = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int c0 = cq<D>(i, 0), c1 = cq<D>(i, 1), c2 = cq<D>(i, 2);
+    if (c0 > 0) j[0] += f[i]; else if (c0 < 0) j[0] -= f[i];
+    if (c1 > 0) j[1] += f[i]; else if (c1 < 0) j[1] -= f[i];
+    if (c2 > 0) j[2] += f[i]; else if (c2 < 0) j[2] -= f[i];
+    if (c0 != 0) Pi[0] += f[i];
+    if (c1 != 0) Pi[1] += f[i];
+    if (c2 != 0) Pi[2] += f[i];
+    if (c0 * c1 > 0) Pi[3] += f[i]; else if (c0 * c1 < 0) Pi[3] -= f[i];
+    if (c0 * c2 > 0) Pi[4] += f[i]; else if (c0 * c2 < 0) Pi[4] -= f[i];
+    if (c1 * c2 > 0) Pi[5] += f[i]; else if (c1 * c2 < 0) Pi[5] -= f[i];
+  }
+}
+
+// Peng-Robinson pressure, Eq. (PREoS).
+template <typename T>
+__device__ __forceinline__ T pr_pressure(const DevDomain& d, T rho) {
+  const T b = (T)d.b;
+  return rho * (T)d.RT / ((T)1 - b * rho) - (T)d.aalpha * rho * rho / ((T)1 + (T)2 * b * rho - b * b * rho * rho);
+}
+
+// Signed pseudo-potential s*psi, psi = sqrt|P - P0|, s = +1 if P > P0 else -1 (Sec. 2.3).
+// The sign travels in the sign bit (-0 when P == P0).
+template <typename R>
+__device__ __forceinline__ R signed_psi(const DevDomain& d, R rho) {
+  double dd;
+  if (sizeof(R) == 8 || d.eos_fp64 == 2 || (d.eos_fp64 == 1 && (double)rho > d.band_lo && (double)rho < d.band_hi)) {
+    const double r = (double)rho;
+    dd = pr_pressure<double>(d, r) - r * (1.0 / 3.0);
+    const double ps = sqrt(fabs(dd));
+    return (R)(dd > 0.0 ? ps : -ps);
+  }
+  const float r = (float)rho;
+  const float df = pr_pressure<float>(d, r) - r * (1.0f / 3.0f);
+  const float ps = sqrtf(fabsf(df));
+  return (R)(df > 0.0f ? ps : -ps);
+}
+
+template <typename R>
+__device__ __forceinline__ R omega_of(const DevDomain& d, R rho) {
+  R phi = (rho - (R)d.rho_v) * (R)d.inv_drho;
+  phi = phi < (R)0 ? (R)0 : (phi > (R)1 ? (R)1 : phi);
+  const R nu = (R)d.nu_v + phi * (R)d.dnu;
+  return (R)1 / ((R)3 * nu + (R)0.5);
+}
+
+}  // namespace lbm

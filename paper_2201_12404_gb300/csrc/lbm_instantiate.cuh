@@ -1,0 +1,49 @@
+// Instantiates the launch table for one lattice dimension (included once per
+// lattice translation unit so that the two lattices compile in parallel).
+#pragma once
+
+#include "lbm_kernels.cuh"
+#include "lbm_ops.h"
+
+namespace lbm {
+
+template <int D, typename S, typename R, typename A>
+struct Launch {
+  static dim3 node_grid(const DevDomain& d) {
+    return dim3((d.nx + Blocks<D>::bx - 1) / Blocks<D>::bx, (d.ny + Blocks<D>::by - 1) / Blocks<D>::by,
+                (d.nz + Blocks<D>::bz - 1) / Blocks<D>::bz);
+  }
+  static void moments_eos(const DevDomain& d, int parity, cudaStream_t s) {
+    dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
+    dim3 grd((d.px + blk.x - 1) / blk.x, (d.py + blk.y - 1) / blk.y, (d.pz + blk.z - 1) / blk.z);
+    moments_eos_kernel<D, S, R, A><<<grd, blk, 0, s>>>(d, parity);
+  }
+  static void collide_stream(const DevDomain& d, int parity, cudaStream_t s) {
+    dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
+    collide_stream_kernel<D, S, R, A><<<node_grid(d), blk, 0, s>>>(d, parity);
+  }
+  static unsigned blocks1d(const DevDomain& d) { return (unsigned)((d.N + 255) / 256); }
+  static void init_equilibrium(const DevDomain& d, const double* rho, const double* ux, const double* uy,
+                               const double* uz, cudaStream_t s) {
+    init_equilibrium_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, rho, ux, uy, uz);
+  }
+  static void canonical_read(const DevDomain& d, int parity, double* out, cudaStream_t s) {
+    canonical_read_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, out);
+  }
+  static void canonical_write(const DevDomain& d, const double* in, cudaStream_t s) {
+    canonical_write_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, in);
+  }
+  static void macroscopic(const DevDomain& d, int parity, double* rho, double* u, cudaStream_t s) {
+    macroscopic_kernel<D, S, R, A><<<blocks1d(d), 256, 0, s>>>(d, parity, rho, u);
+  }
+  static int diag_partial(const DevDomain& d, int parity, double* partial, cudaStream_t s) {
+    diag_partial_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, partial);
+    return (int)blocks1d(d);
+  }
+  static Ops table() {
+    return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
+               &canonical_read, &canonical_write, &macroscopic, &diag_partial};
+  }
+};
+
+}  // namespace lbm

@@ -1,0 +1,344 @@
+// Kernels of one time step and of the field I/O, templated on the lattice
+// dimension D, the population storage type S and the arithmetic type R.
+//
+//  moments_eos_kernel    (pass 1)  gather f, form rho and j, evaluate the
+//                                  Peng-Robinson pseudo-potential and q = rho u^3;
+//                                  writes the padded auxiliary fields, ghosts included.
+//  collide_stream_kernel (pass 2)  gather f, force from the auxiliary halo
+//                                  (Eq. Kforce_final), Phi (Eq. correction), f^eq and
+//                                  f* (Eqs. LBMeq, LBMstar), k/s/h split (Appendix A),
+//                                  gamma (Sec. 2.4), relaxation (Eq. LBGK), A-A write.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Pass 1: one thread per padded auxiliary node.  A ghost node evaluates the
+// interior node it images (periodic wrap or mirror across a half-way wall);
+// q is negated across a wall (no-slip image).
+// ---------------------------------------------------------------------------
+template <int D, typename S, typename R, typename A>
+__global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d, int parity) {
+  constexpr int Q = Lattice<D>::Q;
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yp = blockIdx.y * blockDim.y + threadIdx.y;
+  const int zp = blockIdx.z * blockDim.z + threadIdx.z;
+  if (xp >= d.px || yp >= d.py || zp >= d.pz) return;
+  bool flip = false;
+  auto image = [&](int c, int n, int wlo, int whi) {
+    int t = c - 2;
+    if (t < 0) { if (wlo) { t = -1 - t; flip = true; } else t += n; }
+    else if (t >= n) { if (whi) { t = 2 * n - 1 - t; flip = true; } else t -= n; }
+    return t;
+  };
+  const int x = image(xp, d.nx, d.wall_lo[0], d.wall_hi[0]);
+  const int y = image(yp, d.ny, d.wall_lo[1], d.wall_hi[1]);
+  const int z = D == 3 ? image(zp, d.nz, d.wall_lo[2], d.wall_hi[2]) : 0;
+
+  R f[Q];
+  gather<D, S, R>(d, parity, x, y, z, f);
+  R rho, j[3], Pi[6];
+  moments<D, R>(f, rho, j, Pi);
+  if (!(rho > (R)0) || !isfinite((double)rho)) atomicOr(d.flags, 1u);
+
+  A* aux = (A*)d.aux;
+  const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * (long long)zp);
+  aux[pn] = (A)rho;
+  aux[d.PN + pn] = (A)signed_psi<R>(d, rho);
+  // q_a = rho u_a (u_a^2 + 3 P0/rho - 3 cs^2) = rho u_a^3 since P0/rho = cs^2
+  const R inv = (R)1 / rho;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const R ua = j[a] * inv;
+    const R q = rho * ua * ua * ua;
+    aux[(2 + a) * d.PN + pn] = (A)(flip ? -q : q);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: one thread per interior node.
+// ---------------------------------------------------------------------------
+template <int D, typename S, typename R, typename A>
+__global__ void __launch_bounds__(256) collide_stream_kernel(DevDomain d, int parity) {
+  constexpr int Q = Lattice<D>::Q;
+  constexpr R cs2 = (R)(1.0 / 3.0);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = D == 3 ? blockIdx.z * blockDim.z + threadIdx.z : 0;
+  if (x >= d.nx || y >= d.ny || z >= d.nz) return;
+
+  R f[Q];
+  gather<D, S, R>(d, parity, x, y, z, f);
+  R rho, j[3], Pi[6];
+  moments<D, R>(f, rho, j, Pi);
+  const R inv_rho = (R)1 / rho;
+  R u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = j[a] * inv_rho;
+
+  // ---- force, Eq. (Kforce_final), physical sign:
+  //      dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g
+  const A* a_rho = (const A*)d.aux;
+  const A* a_psi = a_rho + d.PN;
+  const long long pc = pnode_of<D>(d, x, y, z);
+  const long long sy = d.px, sz = (long long)d.px * d.py;
+  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (i == Lattice<D>::REST) continue;
+    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
+    const R psi1 = fabs((R)a_psi[pc + o]), psi2 = fabs((R)a_psi[pc + 2 * o]);
+    const R r1 = (R)a_rho[pc + o], r2 = (R)a_rho[pc + 2 * o];
+    const R t4 = (R)(4.0 / 3.0) * psi1 - (R)(1.0 / 6.0) * psi2;
+    const R t3 = (R)2 * r1 - r2;
+    const R W = (R)(3.0 * wq<D>(i));  // w_i / cs^2
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int c = cq<D>(i, a);
+      if (c > 0) { g4[a] += W * t4; g3[a] += W * t3; }
+      else if (c < 0) { g4[a] -= W * t4; g3[a] -= W * t3; }
+    }
+  }
+  const R spsi_c = (R)a_psi[pc];
+  R F[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    F[a] = -((R)2 * spsi_c * g4[a] + (R)d.kappa * rho * g3[a]) + rho * (R)d.g[a];
+
+  // ---- Phi_aa = (1 - omega/2) d_a q_a, central difference (Eq. correction)
+  const R om = omega_of<R>(d, rho);
+  R Phi[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const A* qa = a_rho + (2 + a) * d.PN;
+    const long long e = a == 0 ? 1 : (a == 1 ? sy : sz);
+    Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc + e] - (R)qa[pc - e]) * (R)0.5;
+  }
+
+  // ---- one-dimensional factors: equilibrium X (Psi at xi = u, zeta = cs^2 + u^2),
+  //      extended equilibrium Xs (xi* = u + F/rho, zeta* = cs^2 + xi*^2 + Phi/rho),
+  //      first-order dual d1 of the central Hermite basis; index c+1.
+  R X[3][3], Xs[3][3], d1[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      const R ua = u[a], u2 = ua * ua;
+      X[a][1] = (R)1 - cs2 - u2;
+      X[a][2] = (R)0.5 * (cs2 + u2 + ua);
+      X[a][0] = (R)0.5 * (cs2 + u2 - ua);
+      const R xi = ua + F[a] * inv_rho;
+      const R ze = cs2 + xi * xi + Phi[a] * inv_rho;
+      Xs[a][1] = (R)1 - ze;
+      Xs[a][2] = (R)0.5 * (ze + xi);
+      Xs[a][0] = (R)0.5 * (ze - xi);
+      d1[a][1] = (R)-2 * ua;
+      d1[a][2] = ua + (R)0.5;
+      d1[a][0] = ua - (R)0.5;
+    } else {
+      X[a][0] = X[a][2] = Xs[a][0] = Xs[a][2] = d1[a][0] = d1[a][1] = d1[a][2] = 0;
+      X[a][1] = Xs[a][1] = 1;
+    }
+  }
+  // second-order central Hermite moments: a_ab = Pi_ab - rho u_a u_b, a_aa = Pi_aa - rho u_a^2 - rho cs^2;
+  // the shear part keeps the off-diagonals and the deviatoric diagonal a_aa - trace/D
+  const R axy = Pi[3] - rho * u[0] * u[1];
+  const R axz = D == 3 ? Pi[4] - rho * u[0] * u[2] : (R)0;
+  const R ayz = D == 3 ? Pi[5] - rho * u[1] * u[2] : (R)0;
+  R adiag[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) adiag[a] = a < D ? Pi[a] - rho * u[a] * u[a] - rho * cs2 : (R)0;
+  const R tr = (adiag[0] + adiag[1] + adiag[2]) * (R)(1.0 / D);
+  R dev[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dev[a] = a < D ? adiag[a] - tr : (R)0;
+
+  // ---- per population: f^eq, f*, s (shear part), h = f - f^eq - s; entropic sums
+  // d2 (second-order dual): -1 at c = 0, 1/2 at c = +-1
+  R h[Q];
+  R sA = 0, sB = 0;
+  bool neg = false;
+#pragma unroll
+  for (int iz = 0; iz < (D == 3 ? 3 : 1); ++iz) {
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy) {
+      const R Z0 = D == 3 ? X[2][iz] : (R)1, Zs = D == 3 ? Xs[2][iz] : (R)1;
+      const R Z1 = D == 3 ? d1[2][iz] : (R)0;
+      const R Z2 = D == 3 ? (iz == 1 ? (R)-1 : (R)0.5) : (R)0;
+      const R Y0 = X[1][iy], Y1 = d1[1][iy], Y2 = iy == 1 ? (R)-1 : (R)0.5;
+      const R ryz = rho * Y0 * Z0;
+      const R rsyz = rho * Xs[1][iy] * Zs;
+      // s(cx) = d0(cx) C0 + d1(cx) C1 + d2(cx) C2
+      const R C0 = ayz * Y1 * Z1 + dev[1] * Y2 * Z0 + (D == 3 ? dev[2] * Y0 * Z2 : (R)0);
+      const R C1 = axy * Y1 * Z0 + (D == 3 ? axz * Y0 * Z1 : (R)0);
+      const R C2 = dev[0] * Y0 * Z0;
+#pragma unroll
+      for (int ix = 0; ix < 3; ++ix) {
+        const int i = ix + 3 * iy + 9 * iz;
+        const R feq = ryz * X[0][ix];
+        const R fst = rsyz * Xs[0][ix];
+        const R s = X[0][ix] * C0 + d1[0][ix] * C1 + (ix == 1 ? -C2 : (R)0.5 * C2);
+        const R hh = f[i] - feq - s;
+        neg |= !(fst > (R)0);
+        const R ir = (R)1 / fst;
+        sA += s * hh * ir;
+        sB += hh * hh * ir;
+        f[i] = f[i] - om * s + (fst - feq);
+        h[i] = hh;
+      }
+    }
+  }
+
+  // ---- gamma/2 = 1/omega - (1 - 1/omega) <ds|dh>/<dh|dh>, ds = -s, dh = -h (Sec. 2.4);
+  //      the ratio is formed in float64
+  R gamma;
+  if (d.gamma_mode == 1) {
+    gamma = (R)d.gamma_value;
+  } else if (neg) {
+    gamma = (R)2;
+    atomicAdd(d.guards, 1ull);
+  } else {
+    const double B = (double)sB;
+    const double ratio = B > (sizeof(R) == 8 ? 1e-300 : 1e-37) ? (double)sA / B : 0.0;
+    const double iom = 1.0 / (double)om;
+    gamma = (R)(2.0 * iom - (2.0 - 2.0 * iom) * ratio);
+  }
+  if (d.gamma_out) d.gamma_out[node_of(d, x, y, z)] = (float)gamma;
+
+  // ---- f'_i = f_i - omega s_i - (omega gamma/2) h_i + f*_i - f^eq_i, then stream
+  const R ch = (R)0.5 * om * gamma;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] -= ch * h[i];
+  scatter<D, S, R>(d, parity, x, y, z, f);
+}
+
+// ---------------------------------------------------------------------------
+// f := f^eq(rho, u) at every node (natural layout, parity 0).
+// ---------------------------------------------------------------------------
+template <int D, typename S>
+__global__ void init_equilibrium_kernel(DevDomain d, const double* rho, const double* ux,
+                                        const double* uy, const double* uz) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  const double r = rho[n];
+  const double u[3] = {ux[n], uy[n], D == 3 ? uz[n] : 0.0};
+  double X[3][3];
+  for (int a = 0; a < 3; ++a) {
+    const double u2 = u[a] * u[a];
+    X[a][1] = a < D ? 1.0 - 1.0 / 3.0 - u2 : 1.0;
+    X[a][2] = a < D ? 0.5 * (1.0 / 3.0 + u2 + u[a]) : 0.0;
+    X[a][0] = a < D ? 0.5 * (1.0 / 3.0 + u2 - u[a]) : 0.0;
+  }
+  S* F = (S*)d.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    st_pop<S, double>(F + (long long)i * d.N + n, r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1]);
+}
+
+// ---------------------------------------------------------------------------
+// Canonical (post-stream, pre-collision) populations <-> float64 buffer.
+// ---------------------------------------------------------------------------
+template <int D, typename S>
+__global__ void canonical_read_kernel(DevDomain d, int parity, double* out) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+  double f[Q];
+  gather<D, S, double>(d, parity, x, y, z, f);
+  for (int i = 0; i < Q; ++i) out[(long long)i * d.N + n] = f[i];
+}
+
+template <int D, typename S>
+__global__ void canonical_write_kernel(DevDomain d, const double* in) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  S* F = (S*)d.f;
+  for (int i = 0; i < Q; ++i) st_pop<S, double>(F + (long long)i * d.N + n, in[(long long)i * d.N + n]);
+}
+
+// ---------------------------------------------------------------------------
+// Density and exact-difference-method velocity u + F/(2 rho); the auxiliary
+// fields must describe the current state (pass 1 run just before).
+// ---------------------------------------------------------------------------
+template <int D, typename S, typename R, typename A>
+__global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, double* u_out) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+  R f[Q];
+  gather<D, S, R>(d, parity, x, y, z, f);
+  R rho, j[3], Pi[6];
+  moments<D, R>(f, rho, j, Pi);
+  const A* a_rho = (const A*)d.aux;
+  const A* a_psi = a_rho + d.PN;
+  const long long pc = pnode_of<D>(d, x, y, z);
+  const long long sy = d.px, sz = (long long)d.px * d.py;
+  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
+  for (int i = 0; i < Q; ++i) {
+    if (i == Lattice<D>::REST) continue;
+    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
+    const R t4 = (R)(4.0 / 3.0) * fabs((R)a_psi[pc + o]) - (R)(1.0 / 6.0) * fabs((R)a_psi[pc + 2 * o]);
+    const R t3 = (R)2 * (R)a_rho[pc + o] - (R)a_rho[pc + 2 * o];
+    const R W = (R)(3.0 * wq<D>(i));
+    for (int a = 0; a < D; ++a) {
+      const int c = cq<D>(i, a);
+      g4[a] += W * (R)c * t4;
+      g3[a] += W * (R)c * t3;
+    }
+  }
+  rho_out[n] = (double)rho;
+  for (int a = 0; a < D; ++a) {
+    const R Fa = -((R)2 * (R)a_psi[pc] * g4[a] + (R)d.kappa * rho * g3[a]) + rho * (R)d.g[a];
+    u_out[a * d.N + n] = (double)((j[a] + (R)0.5 * Fa) / rho);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic totals: per-block partial sums (fixed order), then one block.
+// partial layout: [block][5] = mass, jx, jy, jz, max|u|.
+// ---------------------------------------------------------------------------
+template <int D, typename S>
+__global__ void __launch_bounds__(256) diag_partial_kernel(DevDomain d, int parity, double* partial) {
+  constexpr int Q = Lattice<D>::Q;
+  __shared__ double sh[5][256];
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0, jj[3] = {0, 0, 0}, um = 0;
+  if (n < d.N) {
+    const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+    double f[Q];
+    gather<D, S, double>(d, parity, x, y, z, f);
+    double Pi[6];
+    moments<D, double>(f, m, jj, Pi);
+    const double u2 = (jj[0] * jj[0] + jj[1] * jj[1] + jj[2] * jj[2]) / (m * m);
+    um = sqrt(u2);
+  }
+  sh[0][threadIdx.x] = m; sh[1][threadIdx.x] = jj[0]; sh[2][threadIdx.x] = jj[1];
+  sh[3][threadIdx.x] = jj[2]; sh[4][threadIdx.x] = um;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+      sh[4][threadIdx.x] = fmax(sh[4][threadIdx.x], sh[4][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) partial[blockIdx.x * 5 + k] = sh[k][0];
+}
+
+static __global__ void diag_final_kernel(const double* partial, int nblocks, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b) {
+    for (int k = 0; k < 4; ++k) acc[k] += partial[b * 5 + k];
+    acc[4] = fmax(acc[4], partial[b * 5 + 4]);
+  }
+  for (int k = 0; k < 5; ++k) out[k] = acc[k];
+}
+
+}  // namespace lbm

@@ -1,0 +1,36 @@
+// Launch table of one (lattice, precision) instantiation of the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct Ops {
+  int D, Q;
+  size_t pop_bytes;  // bytes per stored population
+  size_t aux_bytes;  // bytes per auxiliary value
+  void (*moments_eos)(const DevDomain&, int parity, cudaStream_t);
+  void (*collide_stream)(const DevDomain&, int parity, cudaStream_t);
+  void (*init_equilibrium)(const DevDomain&, const double* rho, const double* ux, const double* uy,
+                           const double* uz, cudaStream_t);
+  void (*canonical_read)(const DevDomain&, int parity, double* out, cudaStream_t);
+  void (*canonical_write)(const DevDomain&, const double* in, cudaStream_t);
+  void (*macroscopic)(const DevDomain&, int parity, double* rho, double* u, cudaStream_t);
+  // returns the number of partial blocks written to partial (5 doubles each)
+  int (*diag_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
+};
+
+// Defined in lbm_d2q9.cu and lbm_d3q27.cu.
+extern const Ops ops_d2q9_fp64, ops_d2q9_fp32, ops_d3q27_fp64, ops_d3q27_fp32;
+
+// Final fixed-order reduction of the diagnostic partial sums (lbm_d2q9.cu).
+void launch_diag_final(const double* partial, int nblocks, double* out, cudaStream_t s);
+
+// Block shape of the per-node kernels (x fastest).
+template <int D> struct Blocks;
+template <> struct Blocks<2> { static constexpr int bx = 64, by = 4, bz = 1; };
+template <> struct Blocks<3> { static constexpr int bx = 32, by = 4, bz = 2; };
+
+}  // namespace lbm

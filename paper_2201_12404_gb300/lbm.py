@@ -1,0 +1,253 @@
+"""ctypes binding of liblbm.so (C ABI in include/lbm.h), same names as the C calls.
+
+Only argument marshalling lives here: every step of the lattice Boltzmann path
+runs in the CUDA kernels of the library.  The library must have been built
+(``python -m paper_2201_12404_gb300.build`` or ``__graft_entry__.build()``);
+there is no fallback, and loading fails loudly when it is missing.
+
+Arrays: numpy float64, field arrays shaped (nz, ny, nx) (nz = 1 in 2-D) or flat;
+populations shaped (Q, nz, ny, nx) or flat, canonical order i = (cx+1) + 3(cy+1)
++ 9(cz+1).  Torch tensors on the host are accepted through ``.numpy()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
+LBM_D2Q9, LBM_D3Q27 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
+LBM_GAMMA_ENTROPIC, LBM_GAMMA_FIXED = 0, 1
+
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
+                4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+
+
+class lbm_params(ctypes.Structure):
+    """Mirror of lbm_params in include/lbm.h."""
+
+    _fields_ = [
+        ("lattice", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
+        ("T_over_Tc", ctypes.c_double), ("acentric", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("nu_liquid", ctypes.c_double), ("nu_vapour", ctypes.c_double),
+        ("rho_liquid", ctypes.c_double), ("rho_vapour", ctypes.c_double),
+        ("body_force", ctypes.c_double * 3),
+        ("bc", ctypes.c_int32 * 6),
+        ("gamma_mode", ctypes.c_int32), ("gamma_value", ctypes.c_double),
+        ("eos_fp64", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load():
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                                  "(python -m paper_2201_12404_gb300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            H = ctypes.c_void_p
+            P = ctypes.POINTER(lbm_params)
+            st = ctypes.c_int
+            sig = {
+                "lbm_default_params": (st, [P]),
+                "lbm_create_domain": (st, [P, ctypes.POINTER(H)]),
+                "lbm_init_fields": (st, [H, _dp, _dp, _dp, _dp]),
+                "lbm_step": (st, [H, ctypes.c_int64]),
+                "lbm_synchronize": (st, [H]),
+                "lbm_read_macroscopic": (st, [H, _dp, _dp, _dp, _dp]),
+                "lbm_destroy": (st, [H]),
+                "lbm_read_populations": (st, [H, _dp, ctypes.c_size_t]),
+                "lbm_write_populations": (st, [H, _dp, ctypes.c_size_t]),
+                "lbm_read_diag": (st, [H, _dp, _dp, _dp, _dp]),
+                "lbm_record_gamma": (st, [H, ctypes.c_int]),
+                "lbm_guard_count": (st, [H, ctypes.POINTER(ctypes.c_uint64)]),
+                "lbm_footprint_bytes": (ctypes.c_size_t, [P]),
+                "lbm_coexistence": (st, [P, _dp, _dp, _dp]),
+                "lbm_set_timing": (st, [H, ctypes.c_int]),
+                "lbm_kernel_times": (st, [H, _dp, ctypes.POINTER(ctypes.c_int64)]),
+                "lbm_launch_count": (ctypes.c_int64, [H]),
+                "lbm_last_error": (ctypes.c_char_p, [H]),
+                "lbm_version": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _check(status, handle=None):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(handle).decode()
+        raise LBMError(status, msg)
+
+
+def lbm_default_params(**overrides) -> lbm_params:
+    p = lbm_params()
+    _check(load().lbm_default_params(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if k in ("body_force", "bc"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def lbm_footprint_bytes(p: lbm_params) -> int:
+    return int(load().lbm_footprint_bytes(ctypes.byref(p)))
+
+
+def lbm_coexistence(p: lbm_params):
+    rv, rl, ps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_coexistence(ctypes.byref(p), ctypes.byref(rv), ctypes.byref(rl), ctypes.byref(ps)))
+    return rv.value, rl.value, ps.value
+
+
+def lbm_version() -> str:
+    return load().lbm_version().decode()
+
+
+class Domain:
+    """One simulation domain (owns an lbm_handle)."""
+
+    def __init__(self, params: lbm_params):
+        L = load()
+        self.params = params
+        self.D = 3 if params.lattice == LBM_D3Q27 else 2
+        self.Q = 27 if self.D == 3 else 9
+        self.shape = (params.nz if self.D == 3 else 1, params.ny, params.nx)
+        self.N = int(np.prod(self.shape))
+        h = ctypes.c_void_p()
+        _check(L.lbm_create_domain(ctypes.byref(params), ctypes.byref(h)), None)
+        self.handle = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().lbm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, status):
+        _check(status, self.handle)
+
+    def _field(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if a.size != self.N:
+            raise ValueError(f"field has {a.size} values, domain has {self.N}")
+        return a
+
+    # -- C calls
+    def lbm_init_fields(self, rho, u):
+        r = self._field(rho)
+        comps = [self._field(u[a]) for a in range(self.D)]
+        uz = comps[2] if self.D == 3 else None
+        self._c(load().lbm_init_fields(self.handle, _ptr(r), _ptr(comps[0]), _ptr(comps[1]), _ptr(uz)))
+
+    def lbm_init_fields_ptr(self, rho_ptr, ux_ptr, uy_ptr, uz_ptr=None):
+        """Same call with raw host pointers (e.g. pinned torch tensors' data_ptr())."""
+        c = lambda p: ctypes.cast(ctypes.c_void_p(p), _dp) if p else None
+        self._c(load().lbm_init_fields(self.handle, c(rho_ptr), c(ux_ptr), c(uy_ptr), c(uz_ptr)))
+
+    def lbm_step(self, nsteps: int):
+        self._c(load().lbm_step(self.handle, int(nsteps)))
+
+    def lbm_synchronize(self):
+        self._c(load().lbm_synchronize(self.handle))
+
+    def lbm_read_macroscopic(self):
+        rho = np.empty(self.N)
+        u = np.empty((self.D, self.N))
+        self._c(load().lbm_read_macroscopic(self.handle, _ptr(rho), _ptr(u[0]), _ptr(u[1]),
+                                            _ptr(u[2]) if self.D == 3 else None))
+        return rho.reshape(self.shape), u.reshape((self.D,) + self.shape)
+
+    def lbm_read_macroscopic_ptr(self, rho_ptr, ux_ptr, uy_ptr, uz_ptr=None):
+        c = lambda p: ctypes.cast(ctypes.c_void_p(p), _dp) if p else None
+        self._c(load().lbm_read_macroscopic(self.handle, c(rho_ptr), c(ux_ptr), c(uy_ptr), c(uz_ptr)))
+
+    def lbm_read_populations(self):
+        out = np.empty(self.Q * self.N)
+        self._c(load().lbm_read_populations(self.handle, _ptr(out), out.size))
+        return out.reshape((self.Q,) + self.shape)
+
+    def lbm_write_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        if f.size != self.Q * self.N:
+            raise ValueError("populations must hold Q*N values")
+        self._c(load().lbm_write_populations(self.handle, _ptr(f), f.size))
+
+    def lbm_read_diag(self, with_gamma=False):
+        m, mx = ctypes.c_double(), ctypes.c_double()
+        mom = np.zeros(3)
+        g = np.empty(self.N) if with_gamma else None
+        self._c(load().lbm_read_diag(self.handle, ctypes.byref(m), _ptr(mom), ctypes.byref(mx), _ptr(g)))
+        out = dict(mass=m.value, momentum=mom, max_u=mx.value)
+        if with_gamma:
+            out["gamma"] = g.reshape(self.shape)
+        return out
+
+    def lbm_record_gamma(self, enable=True):
+        self._c(load().lbm_record_gamma(self.handle, 1 if enable else 0))
+
+    def lbm_guard_count(self) -> int:
+        c = ctypes.c_uint64()
+        self._c(load().lbm_guard_count(self.handle, ctypes.byref(c)))
+        return int(c.value)
+
+    def lbm_set_timing(self, enable=True):
+        self._c(load().lbm_set_timing(self.handle, 1 if enable else 0))
+
+    def lbm_kernel_times(self):
+        ms = (ctypes.c_double * 2)()
+        cnt = (ctypes.c_int64 * 2)()
+        self._c(load().lbm_kernel_times(self.handle, ms, cnt))
+        return [ms[0], ms[1]], [cnt[0], cnt[1]]
+
+    def lbm_launch_count(self) -> int:
+        return int(load().lbm_launch_count(self.handle))
+
+    def lbm_last_error(self) -> str:
+        return load().lbm_last_error(self.handle).decode()

@@ -1,0 +1,122 @@
+"""The benchmark workloads: parameters and seeded initial fields.
+
+Each workload follows one of the paper's experiments (Sec. 3) at the sizes the
+benchmark uses.  EOS constants are the paper's (a = 0.003, b = 0.095, R = 1,
+acentric 0.344, Sec. 3.1).  The coexistence densities come from the library's
+Maxwell construction (lbm_coexistence); the interface width W and kappa give a
+diffuse interface of about 5 nodes, the width the paper's stability study uses
+(Sec. 3.2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs as I
+
+PAPER_EOS = dict(a=0.003, b=0.095, R=1.0, acentric=0.344)
+
+
+@dataclass
+class Workload:
+    name: str
+    D: int
+    nx: int
+    ny: int
+    nz: int
+    T_over_Tc: float
+    kappa: float
+    nu_liquid: float
+    mu_ratio: float          # mu_l/mu_v; nu_v = nu_l (rho_l/rho_v) / mu_ratio
+    R: float                 # drop radius
+    U: float                 # impact speed
+    film: float              # film thickness / R
+    W: float = 5.0
+    steps: int = 5000
+    walls_axis: int = -1     # bounce-back on both faces of this axis, -1: fully periodic
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+# D3Q27 drop impact on a thin film, 512x512x256, density ratio ~1000 (T/Tc = 0.59)
+DROP_IMPACT_3D = Workload(
+    name="D3Q27 drop impact on a thin film 512x512x256 (rho_l/rho_v ~ 1000, R = 64, U = 0.04, h = 0.2R)",
+    D=3, nx=512, ny=512, nz=256, T_over_Tc=0.59, kappa=0.005, nu_liquid=0.005, mu_ratio=50.0,
+    R=64.0, U=0.04, film=0.2, steps=5000, walls_axis=2)
+
+# D2Q9 drop impact, 2048x1024, Re ~ 2000, We ~ 250
+DROP_IMPACT_2D = Workload(
+    name="D2Q9 drop impact on a thin film 2048x1024 (rho_l/rho_v ~ 1000, R = 128, U = 0.05, h = 0.2R)",
+    D=2, nx=2048, ny=1024, nz=1, T_over_Tc=0.59, kappa=0.005, nu_liquid=0.0064, mu_ratio=50.0,
+    R=128.0, U=0.05, film=0.2, steps=20000, walls_axis=1)
+
+# D2Q9 static drop, 128x128 periodic, T/Tc = 0.8
+STATIC_DROP_2D = Workload(
+    name="D2Q9 static drop 128x128 periodic (T/Tc = 0.8, R = 25)",
+    D=2, nx=128, ny=128, nz=1, T_over_Tc=0.8, kappa=0.002, nu_liquid=0.01, mu_ratio=0.0,
+    R=25.0, U=0.0, film=0.0, steps=2000, walls_axis=-1)
+
+
+# The same drop impact at half the resolution per axis (8.4M nodes, 0.9 GB of FP32
+# populations: still far larger than L2), the case kernel profiles are taken on.
+DROP_IMPACT_3D_SMALL = Workload(
+    name="D3Q27 drop impact on a thin film 256x256x128 (rho_l/rho_v ~ 1000, R = 32, U = 0.04, h = 0.2R)",
+    D=3, nx=256, ny=256, nz=128, T_over_Tc=0.59, kappa=0.005, nu_liquid=0.005, mu_ratio=50.0,
+    R=32.0, U=0.04, film=0.2, steps=5000, walls_axis=2)
+
+WORKLOADS = {"drop3d": DROP_IMPACT_3D, "drop3d-small": DROP_IMPACT_3D_SMALL, "drop2d": DROP_IMPACT_2D,
+             "static2d": STATIC_DROP_2D}
+
+
+def by_name(name: str) -> Workload:
+    return WORKLOADS[name]
+
+
+def coexistence(wl: Workload):
+    from . import lbm
+    p = lbm.lbm_default_params(T_over_Tc=wl.T_over_Tc, **PAPER_EOS)
+    rv, rl, _ = lbm.lbm_coexistence(p)
+    return rv, rl
+
+
+def viscosities(wl: Workload, rv, rl):
+    if wl.mu_ratio <= 0:
+        return wl.nu_liquid, wl.nu_liquid
+    return wl.nu_liquid, wl.nu_liquid * (rl / rv) / wl.mu_ratio
+
+
+def params(wl: Workload, precision, stream=None, rv=None, rl=None):
+    from . import lbm
+    if rv is None:
+        rv, rl = coexistence(wl)
+    nu_l, nu_v = viscosities(wl, rv, rl)
+    bc = [0] * 6
+    if wl.walls_axis >= 0:
+        bc[2 * wl.walls_axis] = bc[2 * wl.walls_axis + 1] = 1
+    return lbm.lbm_default_params(
+        lattice=lbm.LBM_D3Q27 if wl.D == 3 else lbm.LBM_D2Q9, precision=precision,
+        nx=wl.nx, ny=wl.ny, nz=wl.nz, T_over_Tc=wl.T_over_Tc, kappa=wl.kappa,
+        nu_liquid=nu_l, nu_vapour=nu_v, rho_liquid=rl, rho_vapour=rv, bc=bc,
+        stream=stream, **PAPER_EOS)
+
+
+def initial_fields(wl: Workload, rv, rl, seed=I.SEED_BASE, crop=None):
+    """Seeded initial density and velocity.  crop = (nz, ny, nx) evaluates the
+    same geometry on a smaller box (used for bounded CPU samples)."""
+    shape = crop if crop is not None else wl.shape
+    if wl.U > 0 or wl.film > 0:
+        rho, u = I.drop_on_film(shape, wl.D, wl.R * (shape[-1] / wl.nx), wl.film * wl.R * (shape[-1] / wl.nx),
+                                wl.U, rl, rv, wl.W)
+    else:
+        rho = I.drop(shape, (shape[2] / 2, shape[1] / 2, shape[0] / 2), wl.R * (shape[-1] / wl.nx), rl, rv, wl.W, D=wl.D)
+        rho = rho + I.uniform_noise(shape, 1e-6, seed)
+        u = np.zeros((wl.D,) + tuple(shape))
+    return rho, u

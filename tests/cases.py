@@ -1,0 +1,68 @@
+"""Shared test cases: one parameter dictionary feeds both the CUDA library
+(lbm_params) and the oracle (orc_params), plus seeded initial states."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from oracle import thermo
+from paper_2201_12404_gb300 import inputs as I
+from paper_2201_12404_gb300 import lbm
+
+PAPER_EOS = dict(a=0.003, b=0.095, R=1.0, acentric=0.344)
+
+
+def case(D, nx, ny, nz=1, *, Tr=0.8, kappa=0.002, nu_l=0.05, nu_v=0.15, walls=False, g=(0.0, 0.0, 0.0),
+         gamma_mode=0, gamma_value=2.0, precision=lbm.LBM_FP64, eos_fp64=1, rho_l=None, rho_v=None):
+    if rho_l is None:
+        rv, rl, _ = thermo.maxwell(Tr, **PAPER_EOS)
+    else:
+        rv, rl = rho_v, rho_l
+    bc = [0] * 6
+    if walls:
+        ax = 1 if D == 2 else 2
+        bc[2 * ax] = bc[2 * ax + 1] = 1
+    return dict(D=D, nx=nx, ny=ny, nz=nz if D == 3 else 1, Tr=Tr, kappa=kappa, nu_l=nu_l, nu_v=nu_v,
+                rho_l=rl, rho_v=rv, bc=tuple(bc), g=tuple(g), gamma_mode=gamma_mode,
+                gamma_value=gamma_value, precision=precision, eos_fp64=eos_fp64)
+
+
+def oracle_params(c):
+    return O.make_params(c["D"], c["nx"], c["ny"], c["nz"], T_over_Tc=c["Tr"], kappa=c["kappa"],
+                         nu_liquid=c["nu_l"], nu_vapour=c["nu_v"], rho_liquid=c["rho_l"],
+                         rho_vapour=c["rho_v"], g=c["g"], bc=c["bc"], gamma_mode=c["gamma_mode"],
+                         gamma_value=c["gamma_value"], **PAPER_EOS)
+
+
+def lbm_params(c):
+    return lbm.lbm_default_params(
+        lattice=lbm.LBM_D3Q27 if c["D"] == 3 else lbm.LBM_D2Q9, precision=c["precision"],
+        nx=c["nx"], ny=c["ny"], nz=c["nz"], T_over_Tc=c["Tr"], kappa=c["kappa"],
+        nu_liquid=c["nu_l"], nu_vapour=c["nu_v"], rho_liquid=c["rho_l"], rho_vapour=c["rho_v"],
+        body_force=c["g"], bc=c["bc"], gamma_mode=c["gamma_mode"], gamma_value=c["gamma_value"],
+        eos_fp64=c["eos_fp64"], **PAPER_EOS)
+
+
+def shape(c):
+    return (c["nz"], c["ny"], c["nx"])
+
+
+def drop_state(c, seed=11, perturb=0.01, W=5.0):
+    """Oracle equilibrium of a drop (radius a quarter of the smallest side), then
+    every population multiplied by (1 + eps), |eps| <= perturb: a non-equilibrium state."""
+    D = c["D"]
+    sh = shape(c)
+    R = 0.25 * min(x for x in sh if x > 1)
+    centre = (c["nx"] / 2 - 0.3, c["ny"] / 2 + 0.2, c["nz"] / 2 + 0.1)
+    rho = I.drop(sh, centre, R, c["rho_l"], c["rho_v"], W, D=D)
+    u = I.rng(seed).uniform(-0.02, 0.02, (D,) + sh)
+    f = O.init_equilibrium(oracle_params(c), rho, u)
+    return I.perturbed_populations(f, perturb, seed + 1)
+
+
+def rel_err(f_gpu, f_orc, D):
+    """e_i(r) = |f_gpu - f_orc| / (w_i rho(r)), the per-population error scaled by
+    the population's natural size."""
+    w = O.weights(D).reshape((-1, 1, 1, 1))
+    rho = f_orc.sum(axis=0, keepdims=True)
+    return np.abs(f_gpu - f_orc) / (w * rho)

@@ -1,0 +1,117 @@
+"""Host-only checks of the C ABI: the library loads, exports every entry point
+that include/lbm.h declares, validates parameters and solves the Maxwell
+construction on the host (no GPU work is launched here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from oracle import thermo
+from paper_2201_12404_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(lbm.LIB_PATH):
+        from paper_2201_12404_gb300 import build
+        build.build()
+    return lbm.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create_domain", "lbm_init_fields", "lbm_step", "lbm_read_macroscopic", "lbm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (lbm_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(L, n)
+
+
+def test_params_struct_layout_matches_header(L):
+    # offsets of the C struct, computed by the C compiler from the header
+    src = r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "lbm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, a),
+         offsetof(lbm_params, body_force), offsetof(lbm_params, bc), offsetof(lbm_params, gamma_value),
+         offsetof(lbm_params, eos_fp64), offsetof(lbm_params, stream));
+  return 0;
+}
+'''
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        vals = [int(x) for x in subprocess.check_output([exe]).split()]
+    P = lbm.lbm_params
+    assert vals == [ctypes.sizeof(P), P.a.offset, P.body_force.offset, P.bc.offset, P.gamma_value.offset,
+                    P.eos_fp64.offset, P.stream.offset]
+
+
+def test_default_params_and_footprint(L):
+    p = lbm.lbm_default_params()
+    assert (p.lattice, p.precision, p.nx, p.ny, p.nz) == (lbm.LBM_D2Q9, lbm.LBM_FP32, 64, 64, 1)
+    assert (p.a, p.b, p.acentric) == (0.003, 0.095, 0.344)
+    fp = lbm.lbm_footprint_bytes(p)
+    # 9 float32 populations per node plus 4 padded float32 auxiliary fields
+    assert fp >= 9 * 4 * 64 * 64 + 4 * 4 * 68 * 68
+    p3 = lbm.lbm_default_params(lattice=lbm.LBM_D3Q27, nx=512, ny=512, nz=256)
+    assert lbm.lbm_footprint_bytes(p3) > 27 * 4 * 512 * 512 * 256
+    p64 = lbm.lbm_default_params(lattice=lbm.LBM_D3Q27, precision=lbm.LBM_FP64, nx=512, ny=512, nz=256)
+    assert lbm.lbm_footprint_bytes(p64) > 2 * 27 * 4 * 512 * 512 * 256
+
+
+@pytest.mark.parametrize("overrides,needle", [
+    (dict(nx=4), "nx and ny"),
+    (dict(nz=3), "nz must be 1"),
+    (dict(lattice=lbm.LBM_D3Q27, nz=4), "nz must be >= 5"),
+    (dict(precision=7), "precision"),
+    (dict(nu_liquid=0.0), "viscosities"),
+    (dict(rho_vapour=2.0), "rho_liquid > rho_vapour"),
+    (dict(bc=(1, 0, 0, 0, 0, 0)), "pairs"),
+    (dict(kappa=-1.0), "kappa"),
+    (dict(eos_fp64=5), "eos_fp64"),
+    (dict(gamma_mode=3), "gamma_mode"),
+])
+def test_invalid_params_rejected_without_gpu(L, overrides, needle):
+    p = lbm.lbm_default_params(**overrides)
+    assert lbm.lbm_footprint_bytes(p) == 0
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Domain(p)
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    assert needle in str(e.value)
+
+
+@pytest.mark.parametrize("Tr", [0.59, 0.7, 0.8, 0.9, 0.95])
+def test_library_maxwell_matches_oracle(L, Tr):
+    p = lbm.lbm_default_params(T_over_Tc=Tr)
+    rv, rl, ps = lbm.lbm_coexistence(p)
+    orv, orl, ops_ = thermo.maxwell(Tr, a=p.a, b=p.b, R=p.R, acentric=p.acentric)
+    assert rv == pytest.approx(orv, rel=1e-9)
+    assert rl == pytest.approx(orl, rel=1e-10)
+    assert ps == pytest.approx(ops_, rel=1e-9)
+
+
+def test_version_string(L):
+    assert "sm_103a" in lbm.lbm_version()
