@@ -19,6 +19,8 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# extra nvcc flags (e.g. -DLBM_K2_MINBLOCKS_F32=3) for tuning builds
+FLAGS += os.environ.get("LBM_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

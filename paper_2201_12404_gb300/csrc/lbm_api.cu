@@ -13,6 +13,7 @@
 
 using lbm::DevDomain;
 using lbm::Ops;
+using lbm::Phys;
 
 struct lbm_domain {
   lbm_params p{};
@@ -330,21 +331,29 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
     d.wall_lo[a] = active && is_wall(p->bc[2 * a]);
     d.wall_hi[a] = active && is_wall(p->bc[2 * a + 1]);
   }
-  d.kappa = p->kappa;
-  for (int a = 0; a < 3; ++a) d.g[a] = a < s.D ? p->body_force[a] : 0.0;
-  d.nu_v = p->nu_vapour;
-  d.dnu = p->nu_liquid - p->nu_vapour;
-  d.rho_v = p->rho_vapour;
-  d.inv_drho = 1.0 / (p->rho_liquid - p->rho_vapour);
+  Phys<double>& pd = d.pd;
+  pd.kappa = p->kappa;
+  for (int a = 0; a < 3; ++a) pd.g[a] = a < s.D ? p->body_force[a] : 0.0;
+  pd.nu_v = p->nu_vapour;
+  pd.dnu = p->nu_liquid - p->nu_vapour;
+  pd.rho_v = p->rho_vapour;
+  pd.inv_drho = 1.0 / (p->rho_liquid - p->rho_vapour);
   const EosCoeffs e = eos_coeffs(*p);
-  d.RT = e.RT; d.b = e.b; d.aalpha = e.aalpha;
-  d.gamma_mode = p->gamma_mode;
-  d.gamma_value = p->gamma_value;
-  d.eos_fp64 = p->eos_fp64;
+  pd.RT = e.RT; pd.b = e.b; pd.aalpha = e.aalpha;
+  pd.gamma_value = p->gamma_value;
   // interface band: densities between the phases, 1% of the density jump inside each bulk value
   const double span = p->rho_liquid - p->rho_vapour;
-  d.band_lo = p->rho_vapour + 0.01 * span;
-  d.band_hi = p->rho_liquid - 0.01 * span;
+  pd.band_lo = p->rho_vapour + 0.01 * span;
+  pd.band_hi = p->rho_liquid - 0.01 * span;
+  Phys<float>& pf = d.pf;
+  pf.kappa = (float)pd.kappa;
+  for (int a = 0; a < 3; ++a) pf.g[a] = (float)pd.g[a];
+  pf.nu_v = (float)pd.nu_v; pf.dnu = (float)pd.dnu; pf.rho_v = (float)pd.rho_v; pf.inv_drho = (float)pd.inv_drho;
+  pf.RT = (float)pd.RT; pf.b = (float)pd.b; pf.aalpha = (float)pd.aalpha;
+  pf.gamma_value = (float)pd.gamma_value;
+  pf.band_lo = (float)pd.band_lo; pf.band_hi = (float)pd.band_hi;
+  d.gamma_mode = p->gamma_mode;
+  d.eos_fp64 = p->eos_fp64;
 
   auto bail = [&](cudaError_t err, const char* where) {
     g_create_error = std::string(where) + ": " + cudaGetErrorString(err);

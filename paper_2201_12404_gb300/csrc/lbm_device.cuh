@@ -5,10 +5,10 @@
 //   populations  f[i * N + node]          SoA, node = x + nx*(y + ny*z), one A-A buffer
 //   auxiliary    aux[field * PN + pnode]  fields rho, s*psi, q_x, q_y(, q_z); padded by a
 //                                         2-node ghost layer on every axis (2-D: z not padded)
-// The A-A pattern keeps one population buffer: an even step reads and writes the
-// node's own slots (writing direction i into slot Q-1-i), an odd step reads the
-// neighbours' slots and writes back into them, so that after each odd step slot i
-// of node r holds f_i(r) again.
+// The A-A pattern keeps one population buffer: an even step (parity 0) reads and
+// writes the node's own slots (writing direction i into slot Q-1-i), an odd step
+// (parity 1) reads the neighbours' slots and writes back into them, so that after
+// each odd step slot i of node r holds f_i(r) again.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +31,22 @@ template <int D> __host__ __device__ constexpr double wq(int i) {
   return w1d(cxi(i)) * w1d(cyi(i)) * (D == 3 ? w1d(czi(i)) : 1.0);
 }
 
+// Block shape of the per-node kernels (x fastest); the force+collide+stream pass
+// stages a tile of this shape plus a 2-node halo of the auxiliary fields.
+template <int D> struct Blocks;
+template <> struct Blocks<2> { static constexpr int bx = 64, by = 4, bz = 1; };
+template <> struct Blocks<3> { static constexpr int bx = 32, by = 4, bz = 2; };
+
+// Physical parameters in the arithmetic type of a path (filled on the host, so
+// that kernels never convert float64 parameters on the slow float64 pipe).
+template <typename R> struct Phys {
+  R kappa, g[3];
+  R nu_v, dnu, rho_v, inv_drho;  // nu(rho) = nu_v + clamp((rho - rho_v) inv_drho, 0, 1) dnu
+  R RT, b, aalpha;               // Peng-Robinson: P = rho RT/(1 - b rho) - aalpha rho^2/(1 + 2 b rho - b^2 rho^2)
+  R gamma_value;
+  R band_lo, band_hi;            // interface band of densities (float64 EOS inside it when eos_fp64 == 1)
+};
+
 // ---- what a kernel needs to know about a domain (passed by value) ----
 struct DevDomain {
   void* f;             // populations (storage type)
@@ -42,15 +58,15 @@ struct DevDomain {
   int nx, ny, nz;      // nz = 1 in 2-D
   int px, py, pz;      // padded extents (pz = 1 in 2-D)
   int wall_lo[3], wall_hi[3];
-  // physics
-  double kappa, g[3];
-  double nu_v, dnu, rho_v, inv_drho;  // nu(rho) = nu_v + clamp((rho-rho_v)*inv_drho, 0, 1) * dnu
-  double RT, b, aalpha;               // Peng-Robinson: P = rho RT/(1-b rho) - aalpha rho^2/(1+2 b rho-b^2 rho^2)
   int gamma_mode;
-  double gamma_value;
   int eos_fp64;
-  double band_lo, band_hi;            // interface band of densities for eos_fp64 == 1
+  Phys<double> pd;     // parameters for the float64 path and the float64 islands
+  Phys<float> pf;      // the same rounded to float32
 };
+
+template <typename R> __device__ __forceinline__ const Phys<R>& phys(const DevDomain& d);
+template <> __device__ __forceinline__ const Phys<double>& phys<double>(const DevDomain& d) { return d.pd; }
+template <> __device__ __forceinline__ const Phys<float>& phys<float>(const DevDomain& d) { return d.pf; }
 
 // ---- storage conversion ----
 template <typename S, typename R> __device__ __forceinline__ R ld_pop(const S* p) { return (R)(*p); }
@@ -64,7 +80,14 @@ __device__ __forceinline__ long long pnode_of(const DevDomain& d, int x, int y, 
   return (long long)(x + 2) + (long long)d.px * ((long long)(y + 2) + (long long)d.py * (long long)(D == 3 ? z + 2 : 0));
 }
 
-// Neighbour coordinate along one axis: periodic wrap, or -1 when the link crosses a wall.
+// A node whose every lattice link stays inside the domain (no wrap, no wall).
+template <int D>
+__device__ __forceinline__ bool interior(const DevDomain& d, int x, int y, int z) {
+  return x >= 1 && x <= d.nx - 2 && y >= 1 && y <= d.ny - 2 && (D == 2 || (z >= 1 && z <= d.nz - 2));
+}
+
+// Neighbour coordinate along one axis: periodic wrap, or wall = true when the
+// link crosses a bounce-back wall.
 __device__ __forceinline__ int step_axis(int x, int c, int n, int wlo, int whi, bool& wall) {
   int t = x + c;
   if (t < 0) { if (wlo) wall = true; else t += n; }
@@ -72,50 +95,57 @@ __device__ __forceinline__ int step_axis(int x, int c, int n, int wlo, int whi, 
   return t;
 }
 
-// Pre-collision populations of node (x,y,z) for the given A-A parity (0: even
-// step, natural layout; 1: odd step, populations sit reversed at the upstream node).
-template <int D, typename S, typename R>
-__device__ __forceinline__ void gather(const DevDomain& d, int parity, int x, int y, int z, R* f) {
+// Linear offset of the neighbour r + c_i of an interior node.
+template <int D>
+__device__ __forceinline__ long long link_offset(const DevDomain& d, int i) {
+  return (long long)cxi(i) + (long long)d.nx * cyi(i) + (D == 3 ? (long long)d.nx * d.ny * czi(i) : 0ll);
+}
+
+// Slot holding the pre-collision population i of node (x,y,z) at parity P:
+// P = 0: slot i of the node; P = 1: slot Q-1-i of the upstream node r - c_i, or
+// slot i of the node itself when the upstream link crosses a wall.
+template <int D, int P>
+__device__ __forceinline__ long long src_slot(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
+  constexpr int Q = Lattice<D>::Q;
+  if (P == 0) return (long long)i * d.N + n;
+  if (inner) return (long long)(Q - 1 - i) * d.N + n - link_offset<D>(d, i);
+  bool wall = false;
+  const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
+  const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
+  const int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
+  return wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz);
+}
+
+// Slot receiving the post-collision population i of node (x,y,z) at parity P:
+// streaming f_i(r + c_i) <- f'_i(r); half-way bounce-back f_{Q-1-i}(r) <- f'_i(r)
+// when r + c_i lies beyond a wall.
+template <int D, int P>
+__device__ __forceinline__ long long dst_slot(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
+  constexpr int Q = Lattice<D>::Q;
+  if (P == 0) return (long long)(Q - 1 - i) * d.N + n;
+  if (inner) return (long long)i * d.N + n + link_offset<D>(d, i);
+  bool wall = false;
+  const int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
+  const int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
+  const int tz = D == 3 ? step_axis(z, czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
+  return wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz);
+}
+
+template <int D, int P, typename S, typename R>
+__device__ __forceinline__ void gather(const DevDomain& d, int x, int y, int z, R* f) {
   constexpr int Q = Lattice<D>::Q;
   const S* F = (const S*)d.f;
   const long long n = node_of(d, x, y, z);
-  if (parity == 0) {
+  const bool inner = interior<D>(d, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + (long long)i * d.N + n);
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      bool wall = false;
-      int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
-      int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
-      int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-      long long src = wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz);
-      f[i] = ld_pop<S, R>(F + src);
-    }
-  }
+  for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, inner, x, y, z, n, i));
 }
 
-// Write post-collision populations: streaming f_i(r + c_i) <- f'_i(r), half-way
-// bounce-back f_{Q-1-i}(r) <- f'_i(r) when r + c_i lies beyond a wall.
+// Runtime-parity form for the field I/O kernels.
 template <int D, typename S, typename R>
-__device__ __forceinline__ void scatter(const DevDomain& d, int parity, int x, int y, int z, const R* fo) {
-  constexpr int Q = Lattice<D>::Q;
-  S* F = (S*)d.f;
-  const long long n = node_of(d, x, y, z);
-  if (parity == 0) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) st_pop<S, R>(F + (long long)(Q - 1 - i) * d.N + n, fo[i]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      bool wall = false;
-      int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
-      int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
-      int tz = D == 3 ? step_axis(z, czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-      long long dst = wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz);
-      st_pop<S, R>(F + dst, fo[i]);
-    }
-  }
+__device__ __forceinline__ void gather(const DevDomain& d, int parity, int x, int y, int z, R* f) {
+  if (parity == 0) gather<D, 0, S, R>(d, x, y, z, f);
+  else gather<D, 1, S, R>(d, x, y, z, f);
 }
 
 // rho = sum_i f_i (ascending i), j = sum_i c_i f_i, Pi_ab = sum_i c_ia c_ib f_i.
@@ -147,33 +177,32 @@ __device__ __forceinline__ void moments(const R* f, R& rho, R* j, R* Pi) {
 
 // Peng-Robinson pressure, Eq. (PREoS).
 template <typename T>
-__device__ __forceinline__ T pr_pressure(const DevDomain& d, T rho) {
-  const T b = (T)d.b;
-  return rho * (T)d.RT / ((T)1 - b * rho) - (T)d.aalpha * rho * rho / ((T)1 + (T)2 * b * rho - b * b * rho * rho);
+__device__ __forceinline__ T pr_pressure(const Phys<T>& p, T rho) {
+  return rho * p.RT / ((T)1 - p.b * rho) - p.aalpha * rho * rho / ((T)1 + (T)2 * p.b * rho - p.b * p.b * rho * rho);
 }
 
 // Signed pseudo-potential s*psi, psi = sqrt|P - P0|, s = +1 if P > P0 else -1 (Sec. 2.3).
 // The sign travels in the sign bit (-0 when P == P0).
 template <typename R>
 __device__ __forceinline__ R signed_psi(const DevDomain& d, R rho) {
-  double dd;
-  if (sizeof(R) == 8 || d.eos_fp64 == 2 || (d.eos_fp64 == 1 && (double)rho > d.band_lo && (double)rho < d.band_hi)) {
+  if (sizeof(R) == 8 || d.eos_fp64 == 2 ||
+      (d.eos_fp64 == 1 && rho > phys<R>(d).band_lo && rho < phys<R>(d).band_hi)) {
     const double r = (double)rho;
-    dd = pr_pressure<double>(d, r) - r * (1.0 / 3.0);
+    const double dd = pr_pressure<double>(d.pd, r) - r * (1.0 / 3.0);
     const double ps = sqrt(fabs(dd));
     return (R)(dd > 0.0 ? ps : -ps);
   }
   const float r = (float)rho;
-  const float df = pr_pressure<float>(d, r) - r * (1.0f / 3.0f);
+  const float df = pr_pressure<float>(d.pf, r) - r * (1.0f / 3.0f);
   const float ps = sqrtf(fabsf(df));
   return (R)(df > 0.0f ? ps : -ps);
 }
 
 template <typename R>
-__device__ __forceinline__ R omega_of(const DevDomain& d, R rho) {
-  R phi = (rho - (R)d.rho_v) * (R)d.inv_drho;
+__device__ __forceinline__ R omega_of(const Phys<R>& p, R rho) {
+  R phi = (rho - p.rho_v) * p.inv_drho;
   phi = phi < (R)0 ? (R)0 : (phi > (R)1 ? (R)1 : phi);
-  const R nu = (R)d.nu_v + phi * (R)d.dnu;
+  const R nu = p.nu_v + phi * p.dnu;
   return (R)1 / ((R)3 * nu + (R)0.5);
 }
 

@@ -16,11 +16,13 @@ struct Launch {
   static void moments_eos(const DevDomain& d, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
     dim3 grd((d.px + blk.x - 1) / blk.x, (d.py + blk.y - 1) / blk.y, (d.pz + blk.z - 1) / blk.z);
-    moments_eos_kernel<D, S, R, A><<<grd, blk, 0, s>>>(d, parity);
+    if (parity == 0) moments_eos_kernel<D, 0, S, R, A><<<grd, blk, 0, s>>>(d);
+    else moments_eos_kernel<D, 1, S, R, A><<<grd, blk, 0, s>>>(d);
   }
   static void collide_stream(const DevDomain& d, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
-    collide_stream_kernel<D, S, R, A><<<node_grid(d), blk, 0, s>>>(d, parity);
+    if (parity == 0) collide_stream_kernel<D, 0, S, R, A><<<node_grid(d), blk, 0, s>>>(d);
+    else collide_stream_kernel<D, 1, S, R, A><<<node_grid(d), blk, 0, s>>>(d);
   }
   static unsigned blocks1d(const DevDomain& d) { return (unsigned)((d.N + 255) / 256); }
   static void init_equilibrium(const DevDomain& d, const double* rho, const double* ux, const double* uy,

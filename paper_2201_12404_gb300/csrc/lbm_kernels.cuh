@@ -19,8 +19,8 @@ namespace lbm {
 // interior node it images (periodic wrap or mirror across a half-way wall);
 // q is negated across a wall (no-slip image).
 // ---------------------------------------------------------------------------
-template <int D, typename S, typename R, typename A>
-__global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d, int parity) {
+template <int D, int P, typename S, typename R, typename A>
+__global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d) {
   constexpr int Q = Lattice<D>::Q;
   const int xp = blockIdx.x * blockDim.x + threadIdx.x;
   const int yp = blockIdx.y * blockDim.y + threadIdx.y;
@@ -38,10 +38,10 @@ __global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d, int parit
   const int z = D == 3 ? image(zp, d.nz, d.wall_lo[2], d.wall_hi[2]) : 0;
 
   R f[Q];
-  gather<D, S, R>(d, parity, x, y, z, f);
+  gather<D, P, S, R>(d, x, y, z, f);
   R rho, j[3], Pi[6];
   moments<D, R>(f, rho, j, Pi);
-  if (!(rho > (R)0) || !isfinite((double)rho)) atomicOr(d.flags, 1u);
+  if (!(rho > (R)0) || !(rho < (R)INFINITY)) atomicOr(d.flags, 1u);
 
   A* aux = (A*)d.aux;
   const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * (long long)zp);
@@ -57,161 +57,11 @@ __global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d, int parit
   }
 }
 
-// ---------------------------------------------------------------------------
-// Pass 2: one thread per interior node.
-// ---------------------------------------------------------------------------
-template <int D, typename S, typename R, typename A>
-__global__ void __launch_bounds__(256) collide_stream_kernel(DevDomain d, int parity) {
-  constexpr int Q = Lattice<D>::Q;
-  constexpr R cs2 = (R)(1.0 / 3.0);
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = D == 3 ? blockIdx.z * blockDim.z + threadIdx.z : 0;
-  if (x >= d.nx || y >= d.ny || z >= d.nz) return;
+}  // namespace lbm
 
-  R f[Q];
-  gather<D, S, R>(d, parity, x, y, z, f);
-  R rho, j[3], Pi[6];
-  moments<D, R>(f, rho, j, Pi);
-  const R inv_rho = (R)1 / rho;
-  R u[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = j[a] * inv_rho;
+#include "lbm_collide.cuh"
 
-  // ---- force, Eq. (Kforce_final), physical sign:
-  //      dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g
-  const A* a_rho = (const A*)d.aux;
-  const A* a_psi = a_rho + d.PN;
-  const long long pc = pnode_of<D>(d, x, y, z);
-  const long long sy = d.px, sz = (long long)d.px * d.py;
-  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == Lattice<D>::REST) continue;
-    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
-    const R psi1 = fabs((R)a_psi[pc + o]), psi2 = fabs((R)a_psi[pc + 2 * o]);
-    const R r1 = (R)a_rho[pc + o], r2 = (R)a_rho[pc + 2 * o];
-    const R t4 = (R)(4.0 / 3.0) * psi1 - (R)(1.0 / 6.0) * psi2;
-    const R t3 = (R)2 * r1 - r2;
-    const R W = (R)(3.0 * wq<D>(i));  // w_i / cs^2
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int c = cq<D>(i, a);
-      if (c > 0) { g4[a] += W * t4; g3[a] += W * t3; }
-      else if (c < 0) { g4[a] -= W * t4; g3[a] -= W * t3; }
-    }
-  }
-  const R spsi_c = (R)a_psi[pc];
-  R F[3] = {0, 0, 0};
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-    F[a] = -((R)2 * spsi_c * g4[a] + (R)d.kappa * rho * g3[a]) + rho * (R)d.g[a];
-
-  // ---- Phi_aa = (1 - omega/2) d_a q_a, central difference (Eq. correction)
-  const R om = omega_of<R>(d, rho);
-  R Phi[3] = {0, 0, 0};
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const A* qa = a_rho + (2 + a) * d.PN;
-    const long long e = a == 0 ? 1 : (a == 1 ? sy : sz);
-    Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc + e] - (R)qa[pc - e]) * (R)0.5;
-  }
-
-  // ---- one-dimensional factors: equilibrium X (Psi at xi = u, zeta = cs^2 + u^2),
-  //      extended equilibrium Xs (xi* = u + F/rho, zeta* = cs^2 + xi*^2 + Phi/rho),
-  //      first-order dual d1 of the central Hermite basis; index c+1.
-  R X[3][3], Xs[3][3], d1[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a < D) {
-      const R ua = u[a], u2 = ua * ua;
-      X[a][1] = (R)1 - cs2 - u2;
-      X[a][2] = (R)0.5 * (cs2 + u2 + ua);
-      X[a][0] = (R)0.5 * (cs2 + u2 - ua);
-      const R xi = ua + F[a] * inv_rho;
-      const R ze = cs2 + xi * xi + Phi[a] * inv_rho;
-      Xs[a][1] = (R)1 - ze;
-      Xs[a][2] = (R)0.5 * (ze + xi);
-      Xs[a][0] = (R)0.5 * (ze - xi);
-      d1[a][1] = (R)-2 * ua;
-      d1[a][2] = ua + (R)0.5;
-      d1[a][0] = ua - (R)0.5;
-    } else {
-      X[a][0] = X[a][2] = Xs[a][0] = Xs[a][2] = d1[a][0] = d1[a][1] = d1[a][2] = 0;
-      X[a][1] = Xs[a][1] = 1;
-    }
-  }
-  // second-order central Hermite moments: a_ab = Pi_ab - rho u_a u_b, a_aa = Pi_aa - rho u_a^2 - rho cs^2;
-  // the shear part keeps the off-diagonals and the deviatoric diagonal a_aa - trace/D
-  const R axy = Pi[3] - rho * u[0] * u[1];
-  const R axz = D == 3 ? Pi[4] - rho * u[0] * u[2] : (R)0;
-  const R ayz = D == 3 ? Pi[5] - rho * u[1] * u[2] : (R)0;
-  R adiag[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) adiag[a] = a < D ? Pi[a] - rho * u[a] * u[a] - rho * cs2 : (R)0;
-  const R tr = (adiag[0] + adiag[1] + adiag[2]) * (R)(1.0 / D);
-  R dev[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) dev[a] = a < D ? adiag[a] - tr : (R)0;
-
-  // ---- per population: f^eq, f*, s (shear part), h = f - f^eq - s; entropic sums
-  // d2 (second-order dual): -1 at c = 0, 1/2 at c = +-1
-  R h[Q];
-  R sA = 0, sB = 0;
-  bool neg = false;
-#pragma unroll
-  for (int iz = 0; iz < (D == 3 ? 3 : 1); ++iz) {
-#pragma unroll
-    for (int iy = 0; iy < 3; ++iy) {
-      const R Z0 = D == 3 ? X[2][iz] : (R)1, Zs = D == 3 ? Xs[2][iz] : (R)1;
-      const R Z1 = D == 3 ? d1[2][iz] : (R)0;
-      const R Z2 = D == 3 ? (iz == 1 ? (R)-1 : (R)0.5) : (R)0;
-      const R Y0 = X[1][iy], Y1 = d1[1][iy], Y2 = iy == 1 ? (R)-1 : (R)0.5;
-      const R ryz = rho * Y0 * Z0;
-      const R rsyz = rho * Xs[1][iy] * Zs;
-      // s(cx) = d0(cx) C0 + d1(cx) C1 + d2(cx) C2
-      const R C0 = ayz * Y1 * Z1 + dev[1] * Y2 * Z0 + (D == 3 ? dev[2] * Y0 * Z2 : (R)0);
-      const R C1 = axy * Y1 * Z0 + (D == 3 ? axz * Y0 * Z1 : (R)0);
-      const R C2 = dev[0] * Y0 * Z0;
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix) {
-        const int i = ix + 3 * iy + 9 * iz;
-        const R feq = ryz * X[0][ix];
-        const R fst = rsyz * Xs[0][ix];
-        const R s = X[0][ix] * C0 + d1[0][ix] * C1 + (ix == 1 ? -C2 : (R)0.5 * C2);
-        const R hh = f[i] - feq - s;
-        neg |= !(fst > (R)0);
-        const R ir = (R)1 / fst;
-        sA += s * hh * ir;
-        sB += hh * hh * ir;
-        f[i] = f[i] - om * s + (fst - feq);
-        h[i] = hh;
-      }
-    }
-  }
-
-  // ---- gamma/2 = 1/omega - (1 - 1/omega) <ds|dh>/<dh|dh>, ds = -s, dh = -h (Sec. 2.4);
-  //      the ratio is formed in float64
-  R gamma;
-  if (d.gamma_mode == 1) {
-    gamma = (R)d.gamma_value;
-  } else if (neg) {
-    gamma = (R)2;
-    atomicAdd(d.guards, 1ull);
-  } else {
-    const double B = (double)sB;
-    const double ratio = B > (sizeof(R) == 8 ? 1e-300 : 1e-37) ? (double)sA / B : 0.0;
-    const double iom = 1.0 / (double)om;
-    gamma = (R)(2.0 * iom - (2.0 - 2.0 * iom) * ratio);
-  }
-  if (d.gamma_out) d.gamma_out[node_of(d, x, y, z)] = (float)gamma;
-
-  // ---- f'_i = f_i - omega s_i - (omega gamma/2) h_i + f*_i - f^eq_i, then stream
-  const R ch = (R)0.5 * om * gamma;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] -= ch * h[i];
-  scatter<D, S, R>(d, parity, x, y, z, f);
-}
+namespace lbm {
 
 // ---------------------------------------------------------------------------
 // f := f^eq(rho, u) at every node (natural layout, parity 0).
@@ -293,7 +143,7 @@ __global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, dou
   }
   rho_out[n] = (double)rho;
   for (int a = 0; a < D; ++a) {
-    const R Fa = -((R)2 * (R)a_psi[pc] * g4[a] + (R)d.kappa * rho * g3[a]) + rho * (R)d.g[a];
+    const R Fa = -((R)2 * (R)a_psi[pc] * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
     u_out[a * d.N + n] = (double)((j[a] + (R)0.5 * Fa) / rho);
   }
 }

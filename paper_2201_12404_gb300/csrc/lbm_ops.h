@@ -28,9 +28,4 @@ extern const Ops ops_d2q9_fp64, ops_d2q9_fp32, ops_d3q27_fp64, ops_d3q27_fp32;
 // Final fixed-order reduction of the diagnostic partial sums (lbm_d2q9.cu).
 void launch_diag_final(const double* partial, int nblocks, double* out, cudaStream_t s);
 
-// Block shape of the per-node kernels (x fastest).
-template <int D> struct Blocks;
-template <> struct Blocks<2> { static constexpr int bx = 64, by = 4, bz = 1; };
-template <> struct Blocks<3> { static constexpr int bx = 32, by = 4, bz = 2; };
-
 }  // namespace lbm
