@@ -184,6 +184,38 @@ const char* lbm_last_error(lbm_handle h);
 /* Library build string (lattices, precisions, target architecture). */
 const char* lbm_version(void);
 
+/* Allocation-free stepping.  The paper has no counterpart: this call exists for
+ * callers that cannot allocate device memory (a host framework that owns the
+ * whole device pool, a memory-capped process, code that must not enter the
+ * allocator while other work runs).  It advances caller-owned populations by
+ * nsteps time steps exactly as lbm_step does, without any handle and without
+ * any cudaMalloc/cudaFree or allocating library call.
+ *
+ *   p            domain parameters, validated as by lbm_create_domain; p->stream
+ *                is the stream to run on (NULL = the legacy default stream).
+ *   populations  device pointer to Q*N values of the storage type (float32 for
+ *                LBM_FP32, float64 for LBM_FP64) in canonical order (see the
+ *                conventions above); read and overwritten in place.  The caller
+ *                owns it.
+ *   nsteps       even and >= 0, so that the state is in canonical order again on
+ *                return.
+ *
+ * The auxiliary fields between the two passes live in a 16 MiB scratch array
+ * compiled into the library (every GPU that loads the library holds it until
+ * the process exits).  Domains whose (2 + D) padded auxiliary fields,
+ * (nx+4)(ny+4)(nz+4) values each in the storage type, need more than
+ * 16 MiB - 256 B are rejected: for example 64x64x128 D3Q27 in float32 fits,
+ * 128^3 does not; 1000x1000 D2Q9 in float32 fits.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the one array: calls that overlap on
+ * the GPU (two streams, or two host threads) race and corrupt each other.
+ * Asynchronous: returns once the work is enqueued.  No instability check.
+ * Returns LBM_ERR_INVALID_ARG for NULL pointers, invalid parameters, odd or
+ * negative nsteps, or a domain beyond the scratch maximum; LBM_ERR_CUDA if the
+ * symbol lookup or a launch fails. */
+lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, int64_t nsteps);
+
 #ifdef __cplusplus
 }
 #endif

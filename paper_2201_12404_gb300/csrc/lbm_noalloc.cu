@@ -1,0 +1,116 @@
+// lbm_step_noalloc: time steps without any device allocation.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// framework that owns the whole device memory pool, a memory-capped process,
+// or a host thread that must not touch the allocator while other work is in
+// flight.  They hand in the populations they own; the auxiliary fields that the
+// step needs between its two passes (density, signed pseudo-potential, q) live
+// in a fixed scratch array compiled into this library instead of a cudaMalloc.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "../../include/lbm.h"
+#include "lbm_ops.h"
+
+namespace {
+
+// 16 MiB of scratch on every GPU that loads the library, held until exit.  The
+// first 256 bytes hold the error flags and the gamma-guard counter; the
+// auxiliary fields follow.
+constexpr size_t kScratchBytes = size_t(16) << 20;
+constexpr size_t kHeaderBytes = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side handle, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+lbm_status scratch_address(unsigned char** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LBM_ERR_CUDA;
+    g_scratch_addr[dev] = (unsigned char*)ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, int64_t nsteps) {
+  using lbm::DevDomain;
+  using lbm::Ops;
+  if (!p || !populations || nsteps < 0 || (nsteps & 1)) return LBM_ERR_INVALID_ARG;
+  if (lbm_footprint_bytes(p) == 0) return LBM_ERR_INVALID_ARG;  // same checks as lbm_create_domain
+
+  const int D = p->lattice == LBM_D3Q27 ? 3 : 2;
+  const Ops* ops = p->lattice == LBM_D2Q9 ? (p->precision == LBM_FP64 ? &lbm::ops_d2q9_fp64 : &lbm::ops_d2q9_fp32)
+                                          : (p->precision == LBM_FP64 ? &lbm::ops_d3q27_fp64 : &lbm::ops_d3q27_fp32);
+  DevDomain d{};
+  d.N = (long long)p->nx * p->ny * (D == 3 ? p->nz : 1);
+  d.nx = p->nx; d.ny = p->ny; d.nz = D == 3 ? p->nz : 1;
+  d.px = p->nx + 4; d.py = p->ny + 4; d.pz = D == 3 ? p->nz + 4 : 1;
+  d.PN = (long long)d.px * d.py * d.pz;
+  const double aux_bytes = (double)(2 + D) * (double)d.PN * (double)ops->aux_bytes;
+  if (aux_bytes > (double)(kScratchBytes - kHeaderBytes)) return LBM_ERR_INVALID_ARG;  // beyond the scratch maximum
+  if (nsteps == 0) return LBM_OK;
+
+  for (int a = 0; a < 3; ++a) {
+    d.wall_lo[a] = a < D && p->bc[2 * a] == LBM_BC_BOUNCEBACK;
+    d.wall_hi[a] = a < D && p->bc[2 * a + 1] == LBM_BC_BOUNCEBACK;
+  }
+  lbm::Phys<double>& pd = d.pd;
+  pd.kappa = p->kappa;
+  for (int a = 0; a < 3; ++a) pd.g[a] = a < D ? p->body_force[a] : 0.0;
+  pd.nu_v = p->nu_vapour;
+  pd.dnu = p->nu_liquid - p->nu_vapour;
+  pd.rho_v = p->rho_vapour;
+  pd.inv_drho = 1.0 / (p->rho_liquid - p->rho_vapour);
+  const double Tc = 0.0778 * p->a / (0.45724 * p->b * p->R);
+  const double m = 0.37464 + 1.54226 * p->acentric - 0.26992 * p->acentric * p->acentric;
+  const double sq = 1.0 + m * (1.0 - std::sqrt(p->T_over_Tc));
+  pd.RT = p->R * p->T_over_Tc * Tc;
+  pd.b = p->b;
+  pd.aalpha = p->a * sq * sq;
+  pd.gamma_value = p->gamma_value;
+  const double span = p->rho_liquid - p->rho_vapour;
+  pd.band_lo = p->rho_vapour + 0.01 * span;
+  pd.band_hi = p->rho_liquid - 0.01 * span;
+  lbm::Phys<float>& pf = d.pf;
+  pf.kappa = (float)pd.kappa;
+  for (int a = 0; a < 3; ++a) pf.g[a] = (float)pd.g[a];
+  pf.nu_v = (float)pd.nu_v; pf.dnu = (float)pd.dnu; pf.rho_v = (float)pd.rho_v; pf.inv_drho = (float)pd.inv_drho;
+  pf.RT = (float)pd.RT; pf.b = (float)pd.b; pf.aalpha = (float)pd.aalpha;
+  pf.gamma_value = (float)pd.gamma_value;
+  pf.band_lo = (float)pd.band_lo; pf.band_hi = (float)pd.band_hi;
+  d.gamma_mode = p->gamma_mode;
+  d.eos_fp64 = p->eos_fp64;
+
+  unsigned char* scratch = nullptr;
+  lbm_status st = scratch_address(&scratch);
+  if (st != LBM_OK) return st;
+  d.f = populations;
+  d.flags = (unsigned int*)scratch;
+  d.guards = (unsigned long long*)(scratch + 8);
+  d.aux = scratch + kHeaderBytes;
+  d.gamma_out = nullptr;
+
+  cudaStream_t stream = (cudaStream_t)p->stream;
+  // the scratch keeps the previous call's contents: clear the flags and the counter
+  if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return LBM_ERR_CUDA;
+  int parity = 0;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    ops->moments_eos(d, parity, stream);
+    ops->collide_stream(d, parity, stream);
+    parity ^= 1;
+  }
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}

@@ -92,6 +92,7 @@ def load():
                 "lbm_launch_count": (ctypes.c_int64, [H]),
                 "lbm_last_error": (ctypes.c_char_p, [H]),
                 "lbm_version": (ctypes.c_char_p, []),
+                "lbm_step_noalloc": (st, [P, ctypes.c_void_p, ctypes.c_int64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -136,6 +137,14 @@ def lbm_coexistence(p: lbm_params):
 
 def lbm_version() -> str:
     return load().lbm_version().decode()
+
+
+def lbm_step_noalloc(p: lbm_params, populations_ptr: int, nsteps: int) -> None:
+    """Allocation-free stepping of caller-owned device populations (see include/lbm.h)."""
+    st = load().lbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(populations_ptr), int(nsteps))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_step_noalloc failed (invalid parameters, odd nsteps, a domain beyond "
+                           "the 16 MiB scratch, or a CUDA error)")
 
 
 class Domain:
