@@ -106,13 +106,21 @@ def dist_env():
 
 
 def max_over_ranks(x, world):
+    """Largest value over all ranks (the job's wall time is the slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, max_ms):
+    """Weak scaling: every rank advances its own replica, so the job's updates are
+    world x nodes x steps over the slowest rank's time."""
+    return nodes_per_rank * steps * world / (max_ms * 1e-3) / 1e6
 
 
 def barrier(world):
@@ -231,7 +239,7 @@ def run_ours(args):
     kms, kcnt = dom.lbm_kernel_times()
     dom.lbm_set_timing(False)
     clocks = clk.summary()
-    mlups = wl.N * args.steps * world / (ms_max * 1e-3) / 1e6
+    mlups = whole_job_mlups(wl.N, args.steps, world, ms_max)
 
     # ---- end to end through the C ABI with pinned host buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()

@@ -354,6 +354,7 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
   pf.band_lo = (float)pd.band_lo; pf.band_hi = (float)pd.band_hi;
   d.gamma_mode = p->gamma_mode;
   d.eos_fp64 = p->eos_fp64;
+  lbm::fill_slot_offsets(d, s.D);
 
   auto bail = [&](cudaError_t err, const char* where) {
     g_create_error = std::string(where) + ": " + cudaGetErrorString(err);

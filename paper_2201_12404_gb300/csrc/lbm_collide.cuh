@@ -1,29 +1,28 @@
 // Pass 2 of a time step: force + collide + stream, one thread per interior node.
 //
-// A block owns a tile of Blocks<D> nodes.  It first stages the density and the
-// signed pseudo-potential of the tile plus a 2-node halo in shared memory
-// (coalesced rows), then each thread
-//   - gathers its Q pre-collision populations (A-A parity aware),
-//   - forms rho, j, Pi,
+// A block owns a tile of Blocks<D> nodes and stages the density and the signed
+// pseudo-potential of the tile plus a 2-node halo in shared memory.  Each thread
+//   - gathers its Q pre-collision populations (A-A parity aware) into registers,
+//   - forms rho, j, Pi from row sums (the three populations sharing (cy, cz)),
 //   - evaluates the force of Eq. (Kforce_final) with the physical sign from the
 //     staged tile, and Phi of Eq. (correction) from q = rho u^3,
 //   - builds the one-dimensional factors of f^eq (Eq. LBMeq), f* (Eq. LBMstar)
 //     and of the dual basis of the central Hermite moments (Appendix A),
-//   - pass A over the populations: h = f - f^eq - s and the entropic sums
-//     <ds|dh> = sum s h / f*, <dh|dh> = sum h^2 / f*,
+//   - pass A: h = f - f^eq - s per population, the entropic sums
+//     <ds|dh> = sum s h / f*, <dh|dh> = sum h^2 / f*, and the gamma-free part
+//     g = f - omega s + f* - f^eq in place of f; h goes to shared memory,
 //   - gamma from Sec. 2.4, ratio refined to float64 accuracy,
-//   - pass B: recomputes f^eq, f*, s, h per population and writes
-//     f' = f - omega s - (omega gamma/2) h + f* - f^eq straight to its A-A slot.
-// Recomputing the cheap per-population terms in pass B instead of holding h in
-// registers keeps the register count low enough for several blocks per SM.
+//   - pass B: f' = g - (omega gamma/2) h, written to the A-A slots.
+// Nodes whose links all stay inside the domain take a branch with plain
+// offsets for the gather and the write; the others resolve wrap and walls.
 #pragma once
 
 #include "lbm_device.cuh"
 
-// Minimum resident blocks per SM requested from the register allocator: two
-// 256-thread blocks (128 registers) in the float32 path.
+// Minimum resident 256-thread blocks per SM requested from the register
+// allocator in the float32 path.
 #ifndef LBM_K2_MINBLOCKS_F32
-#define LBM_K2_MINBLOCKS_F32 2
+#define LBM_K2_MINBLOCKS_F32 3
 #endif
 #define LBM_K2_MINBLOCKS(R) (sizeof(R) == 4 ? LBM_K2_MINBLOCKS_F32 : 1)
 
@@ -61,34 +60,46 @@ __device__ __forceinline__ R entropic_gamma(R sA, R sB, R om) {
   return (R)(tw - (2.0 - tw) * ratio);
 }
 
+// Dynamic shared memory of the kernel: h_i of every node of the tile.
+template <int D, typename R>
+constexpr size_t collide_dyn_smem() {
+  return (size_t)Lattice<D>::Q * Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz * sizeof(R);
+}
+
 template <int D, int P, typename S, typename R, typename A>
 __global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
 collide_stream_kernel(DevDomain d) {
   constexpr int Q = Lattice<D>::Q;
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
+  constexpr int NT = BX * BY * BZ;
   constexpr int HX = BX + 4, HY = BY + 4, HZ = D == 3 ? BZ + 4 : 1;
   constexpr int HN = HX * HY * HZ;
   constexpr R cs2 = (R)(1.0 / 3.0);
   __shared__ A s_rho[HN];
   __shared__ A s_psi[HN];
+  // higher-order part h_i of every node of the tile, [i][thread] (dynamic: above 48 KB in float64)
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  R* s_h = (R*)smem_dyn;
 
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = D == 3 ? blockIdx.z * BZ : 0;
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const Phys<R>& ph = phys<R>(d);
 
-  // ---- stage rho and s*psi of the tile plus halo (padded coordinates start at the tile origin)
+  // ---- stage rho and s*psi of the tile plus halo, one halo row (fixed y, z) per warp
+  //      at a time; padded coordinates start at the tile origin
   {
     const A* a_rho = (const A*)d.aux;
     const A* a_psi = a_rho + d.PN;
-    for (int k = tid; k < HN; k += BX * BY * BZ) {
-      const int hx = k % HX, hy = (k / HX) % HY, hz = k / (HX * HY);
-      const int xp = x0 + hx, yp = y0 + hy, zp = z0 + hz;
-      if (xp < d.px && yp < d.py && zp < d.pz) {
-        const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * zp);
-        s_rho[k] = a_rho[pn];
-        s_psi[k] = a_psi[pn];
-      } else {
-        s_rho[k] = (A)1;
-        s_psi[k] = (A)0;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < HY * HZ; r += NT / 32) {
+      const int yp = y0 + r % HY, zp = z0 + r / HY;
+      const bool row_ok = yp < d.py && zp < d.pz;
+      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
+#pragma unroll
+      for (int hx = lane; hx < HX; hx += 32) {
+        const bool ok = row_ok && x0 + hx < d.px;
+        s_rho[r * HX + hx] = ok ? a_rho[base + hx] : (A)1;
+        s_psi[r * HX + hx] = ok ? a_psi[base + hx] : (A)0;
       }
     }
   }
@@ -96,41 +107,75 @@ collide_stream_kernel(DevDomain d) {
 
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
   if (x >= d.nx || y >= d.ny || z >= d.nz) return;
+  const long long n = node_of(d, x, y, z);
+  const bool inner = interior<D>(d, x, y, z);
 
-  const Phys<R>& ph = phys<R>(d);
   R f[Q];
-  gather<D, P, S, R>(d, x, y, z, f);
-  R rho, j[3], Pi[6];
-  moments<D, R>(f, rho, j, Pi);
-  const R inv_rho = (R)1 / rho;
-  R u[3];
+  {
+    const S* Fi = (const S*)d.f;
+    if (inner) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = j[a] * inv_rho;
-
-  // ---- force: dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g
-  const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
-  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
+      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(Fi + src_slot<D, P>(d, true, x, y, z, n, i));
+    } else {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == Lattice<D>::REST) continue;
-    const int o = cxi(i) + HX * (cyi(i) + HY * (D == 3 ? czi(i) : 0));
-    const R psi1 = fabs((R)s_psi[sc + o]), psi2 = fabs((R)s_psi[sc + 2 * o]);
-    const R r1 = (R)s_rho[sc + o], r2 = (R)s_rho[sc + 2 * o];
-    const R t4 = (R)(4.0 / 3.0) * psi1 - (R)(1.0 / 6.0) * psi2;
-    const R t3 = (R)2 * r1 - r2;
-    const R W = (R)(3.0 * wq<D>(i));  // w_i / cs^2
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int c = cq<D>(i, a);
-      if (c > 0) { g4[a] += W * t4; g3[a] += W * t3; }
-      else if (c < 0) { g4[a] -= W * t4; g3[a] -= W * t3; }
+      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(Fi + src_slot<D, P>(d, false, x, y, z, n, i));
     }
   }
-  const R spsi_c = (R)s_psi[sc];
-  R F[3] = {0, 0, 0};
+
+  // ---- rho, j, Pi from row sums: r0 = f- + f0 + f+, r1 = f+ - f-, r2 = f+ + f-
+  R rho = 0, jx = 0, jy = 0, jz = 0, Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
 #pragma unroll
-  for (int a = 0; a < D; ++a)
-    F[a] = -((R)2 * spsi_c * g4[a] + ph.kappa * rho * g3[a]) + rho * ph.g[a];
+  for (int row = 0; row < Q / 3; ++row) {
+    const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
+    const R fm = f[3 * row], f0 = f[3 * row + 1], fp = f[3 * row + 2];
+    const R r2 = fm + fp, r0 = r2 + f0, r1 = fp - fm;
+    rho += r0; jx += r1; Pxx += r2;
+    if (cy != 0) { jy += cy > 0 ? r0 : -r0; Pxy += cy > 0 ? r1 : -r1; Pyy += r0; }
+    if (cz != 0) { jz += cz > 0 ? r0 : -r0; Pxz += cz > 0 ? r1 : -r1; Pzz += r0; }
+    if (cy * cz != 0) Pyz += cy * cz > 0 ? r0 : -r0;
+  }
+  const R inv_rho = (R)1 / rho;
+  const R u[3] = {jx * inv_rho, jy * inv_rho, jz * inv_rho};
+
+  // ---- force: dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g, sums over the
+  //      lattice links row by row (rows rolled, the three x-links of a row unrolled)
+  //      with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz)
+  const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
+  R g4x = 0, g4y = 0, g4z = 0, g3x = 0, g3y = 0, g3z = 0;
+#pragma unroll 1
+  for (int row = 0; row < Q / 3; ++row) {
+    const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
+    const R wyz = (cy == 0 ? (R)2 : (R)0.5) * (D == 3 ? (cz == 0 ? (R)(2.0 / 3.0) : (R)(1.0 / 6.0)) : (R)1);
+    const int orow = HX * (cy + HY * cz);
+    const A* pp = s_psi + sc + orow;
+    const A* pr = s_rho + sc + orow;
+    const A* pp2 = s_psi + sc + 2 * orow;
+    const A* pr2 = s_rho + sc + 2 * orow;
+    // t4 and t3 summed over the row with the x weights 1/6, 2/3, 1/6 and signs -1, 0, +1
+    R rowm4, row04, rowp4, rowm3, row03, rowp3;
+    {
+      const R pm = fabs((R)pp[-1]), p0 = fabs((R)pp[0]), pq = fabs((R)pp[1]);
+      const R pm2 = fabs((R)pp2[-2]), p02 = fabs((R)pp2[0]), pq2 = fabs((R)pp2[2]);
+      rowm4 = (R)(4.0 / 3.0) * pm - (R)(1.0 / 6.0) * pm2;
+      row04 = (row == (Q / 3) / 2) ? (R)0 : (R)(4.0 / 3.0) * p0 - (R)(1.0 / 6.0) * p02;
+      rowp4 = (R)(4.0 / 3.0) * pq - (R)(1.0 / 6.0) * pq2;
+      rowm3 = (R)2 * (R)pr[-1] - (R)pr2[-2];
+      row03 = (row == (Q / 3) / 2) ? (R)0 : (R)2 * (R)pr[0] - (R)pr2[0];
+      rowp3 = (R)2 * (R)pr[1] - (R)pr2[2];
+    }
+    // x-component: (+1) - (-1) with weight 1/6; y, z: weighted row sum 1/6, 2/3, 1/6
+    g4x += wyz * (R)(1.0 / 6.0) * (rowp4 - rowm4);
+    g3x += wyz * (R)(1.0 / 6.0) * (rowp3 - rowm3);
+    const R s4 = wyz * ((R)(1.0 / 6.0) * (rowp4 + rowm4) + (R)(2.0 / 3.0) * row04);
+    const R s3 = wyz * ((R)(1.0 / 6.0) * (rowp3 + rowm3) + (R)(2.0 / 3.0) * row03);
+    if (cy != 0) { g4y += cy > 0 ? s4 : -s4; g3y += cy > 0 ? s3 : -s3; }
+    if (D == 3 && cz != 0) { g4z += cz > 0 ? s4 : -s4; g3z += cz > 0 ? s3 : -s3; }
+  }
+  const R spsi_c = (R)s_psi[sc];
+  R F[3];
+  F[0] = -((R)2 * spsi_c * g4x + ph.kappa * rho * g3x) + rho * ph.g[0];
+  F[1] = -((R)2 * spsi_c * g4y + ph.kappa * rho * g3y) + rho * ph.g[1];
+  F[2] = D == 3 ? -((R)2 * spsi_c * g4z + ph.kappa * rho * g3z) + rho * ph.g[2] : (R)0;
 
   // ---- Phi_aa = (1 - omega/2) d_a q_a, central difference
   const R om = omega_of<R>(ph, rho);
@@ -172,21 +217,19 @@ collide_stream_kernel(DevDomain d) {
   }
   // second-order central Hermite moments; the shear part keeps the off-diagonals
   // and the deviatoric diagonal a_aa - trace/D
-  const R axy = Pi[3] - rho * u[0] * u[1];
-  const R axz = D == 3 ? Pi[4] - rho * u[0] * u[2] : (R)0;
-  const R ayz = D == 3 ? Pi[5] - rho * u[1] * u[2] : (R)0;
-  R adiag[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) adiag[a] = a < D ? Pi[a] - rho * u[a] * u[a] - rho * cs2 : (R)0;
-  const R tr = (adiag[0] + adiag[1] + adiag[2]) * (R)(1.0 / D);
-  R dev[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) dev[a] = a < D ? adiag[a] - tr : (R)0;
+  const R axy = Pxy - rho * u[0] * u[1];
+  const R axz = D == 3 ? Pxz - rho * u[0] * u[2] : (R)0;
+  const R ayz = D == 3 ? Pyz - rho * u[1] * u[2] : (R)0;
+  const R adx = Pxx - rho * u[0] * u[0] - rho * cs2;
+  const R ady = Pyy - rho * u[1] * u[1] - rho * cs2;
+  const R adz = D == 3 ? Pzz - rho * u[2] * u[2] - rho * cs2 : (R)0;
+  const R tr = (adx + ady + adz) * (R)(1.0 / D);
+  const R devx = adx - tr, devy = ady - tr, devz = D == 3 ? adz - tr : (R)0;
 
   // Row coefficients for the populations sharing (cy, cz): f^eq = ryz X_x, f* = rsyz Xs_x,
   // s = d0_x C0 + d1_x C1 + d2_x C2 with d2 = {-1 at c = 0, 1/2 at c = +-1}.
   struct Row { R ryz, rsyz, C0, C1, C2; };
-  auto row = [&](int iy, int iz) {
+  auto row_coef = [&](int iy, int iz) {
     const R Z0 = D == 3 ? X[2][iz] : (R)1, Zs = D == 3 ? Xs[2][iz] : (R)1;
     const R Z1 = D == 3 ? d1[2][iz] : (R)0;
     const R Z2 = D == 3 ? (iz == 1 ? (R)-1 : (R)0.5) : (R)0;
@@ -194,20 +237,19 @@ collide_stream_kernel(DevDomain d) {
     Row r;
     r.ryz = rho * Y0 * Z0;
     r.rsyz = rho * Xs[1][iy] * Zs;
-    r.C0 = ayz * Y1 * Z1 + dev[1] * Y2 * Z0 + (D == 3 ? dev[2] * Y0 * Z2 : (R)0);
+    r.C0 = ayz * Y1 * Z1 + devy * Y2 * Z0 + (D == 3 ? devz * Y0 * Z2 : (R)0);
     r.C1 = axy * Y1 * Z0 + (D == 3 ? axz * Y0 * Z1 : (R)0);
-    r.C2 = dev[0] * Y0 * Z0;
+    r.C2 = devx * Y0 * Z0;
     return r;
   };
 
-  // ---- pass A: entropic sums
-  R sA = 0, sB = 0;
-  bool neg = false;
+  // ---- pass A: entropic sums, h to shared memory, g = f - omega s + f* - f^eq in place of f
+  R sA = 0, sB = 0, fmin = (R)1;
 #pragma unroll
   for (int iz = 0; iz < (D == 3 ? 3 : 1); ++iz) {
 #pragma unroll
     for (int iy = 0; iy < 3; ++iy) {
-      const Row r = row(iy, iz);
+      const Row r = row_coef(iy, iz);
 #pragma unroll
       for (int ix = 0; ix < 3; ++ix) {
         const int i = ix + 3 * iy + 9 * iz;
@@ -215,10 +257,12 @@ collide_stream_kernel(DevDomain d) {
         const R fst = r.rsyz * Xs[0][ix];
         const R s = X[0][ix] * r.C0 + d1[0][ix] * r.C1 + (ix == 1 ? -r.C2 : (R)0.5 * r.C2);
         const R hh = f[i] - feq - s;
-        neg |= !(fst > (R)0);
+        fmin = fmin < fst ? fmin : fst;
         const R hr = hh * rcp_fast<R>(fst);
         sA += s * hr;
         sB += hh * hr;
+        s_h[i * NT + tid] = hh;
+        f[i] = f[i] - om * s + (fst - feq);
       }
     }
   }
@@ -226,34 +270,27 @@ collide_stream_kernel(DevDomain d) {
   R gamma;
   if (d.gamma_mode == 1) {
     gamma = ph.gamma_value;
-  } else if (neg) {
+  } else if (!(fmin > (R)0)) {
     gamma = (R)2;
     atomicAdd(d.guards, 1ull);
   } else {
     gamma = entropic_gamma<R>(sA, sB, om);
   }
-  const long long n = node_of(d, x, y, z);
-  const bool inner = interior<D>(d, x, y, z);
-  S* Fo = (S*)d.f;
   if (d.gamma_out) d.gamma_out[n] = (float)gamma;
 
-  // ---- pass B: relax and stream, f' = f - omega s - (omega gamma/2) h + f* - f^eq
+  // ---- pass B: f' = g - (omega gamma/2) h
   const R ch = (R)0.5 * om * gamma;
 #pragma unroll
-  for (int iz = 0; iz < (D == 3 ? 3 : 1); ++iz) {
+  for (int i = 0; i < Q; ++i) f[i] -= ch * s_h[i * NT + tid];
+
+  // ---- stream: A-A write
+  S* Fo = (S*)d.f;
+  if (inner) {
 #pragma unroll
-    for (int iy = 0; iy < 3; ++iy) {
-      const Row r = row(iy, iz);
+    for (int i = 0; i < Q; ++i) st_pop<S, R>(Fo + dst_slot<D, P>(d, true, x, y, z, n, i), f[i]);
+  } else {
 #pragma unroll
-      for (int ix = 0; ix < 3; ++ix) {
-        const int i = ix + 3 * iy + 9 * iz;
-        const R feq = r.ryz * X[0][ix];
-        const R fst = r.rsyz * Xs[0][ix];
-        const R s = X[0][ix] * r.C0 + d1[0][ix] * r.C1 + (ix == 1 ? -r.C2 : (R)0.5 * r.C2);
-        const R hh = f[i] - feq - s;
-        st_pop<S, R>(Fo + dst_slot<D, P>(d, inner, x, y, z, n, i), f[i] - om * s - ch * hh + (fst - feq));
-      }
-    }
+    for (int i = 0; i < Q; ++i) st_pop<S, R>(Fo + dst_slot<D, P>(d, false, x, y, z, n, i), f[i]);
   }
 }
 

@@ -62,6 +62,11 @@ struct DevDomain {
   int eos_fp64;
   Phys<double> pd;     // parameters for the float64 path and the float64 islands
   Phys<float> pf;      // the same rounded to float32
+  // Element offsets, relative to node r's own slot 0, of the slot population i
+  // is read from (src) and written to (dst) at an interior node, per A-A parity:
+  // src[0][i] = i N, src[1][i] = (Q-1-i) N - off(c_i); dst[0][i] = (Q-1-i) N,
+  // dst[1][i] = i N + off(c_i), off(c) = cx + nx cy + nx ny cz.
+  long long src_off[2][27], dst_off[2][27];
 };
 
 template <typename R> __device__ __forceinline__ const Phys<R>& phys(const DevDomain& d);
@@ -95,20 +100,13 @@ __device__ __forceinline__ int step_axis(int x, int c, int n, int wlo, int whi, 
   return t;
 }
 
-// Linear offset of the neighbour r + c_i of an interior node.
-template <int D>
-__device__ __forceinline__ long long link_offset(const DevDomain& d, int i) {
-  return (long long)cxi(i) + (long long)d.nx * cyi(i) + (D == 3 ? (long long)d.nx * d.ny * czi(i) : 0ll);
-}
-
 // Slot holding the pre-collision population i of node (x,y,z) at parity P:
 // P = 0: slot i of the node; P = 1: slot Q-1-i of the upstream node r - c_i, or
 // slot i of the node itself when the upstream link crosses a wall.
 template <int D, int P>
 __device__ __forceinline__ long long src_slot(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
   constexpr int Q = Lattice<D>::Q;
-  if (P == 0) return (long long)i * d.N + n;
-  if (inner) return (long long)(Q - 1 - i) * d.N + n - link_offset<D>(d, i);
+  if (P == 0 || inner) return n + d.src_off[P][i];
   bool wall = false;
   const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
@@ -122,8 +120,7 @@ __device__ __forceinline__ long long src_slot(const DevDomain& d, bool inner, in
 template <int D, int P>
 __device__ __forceinline__ long long dst_slot(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
   constexpr int Q = Lattice<D>::Q;
-  if (P == 0) return (long long)(Q - 1 - i) * d.N + n;
-  if (inner) return (long long)i * d.N + n + link_offset<D>(d, i);
+  if (P == 0 || inner) return n + d.dst_off[P][i];
   bool wall = false;
   const int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
@@ -136,9 +133,13 @@ __device__ __forceinline__ void gather(const DevDomain& d, int x, int y, int z, 
   constexpr int Q = Lattice<D>::Q;
   const S* F = (const S*)d.f;
   const long long n = node_of(d, x, y, z);
-  const bool inner = interior<D>(d, x, y, z);
+  if (interior<D>(d, x, y, z)) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, inner, x, y, z, n, i));
+    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, true, x, y, z, n, i));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, false, x, y, z, n, i));
+  }
 }
 
 // Runtime-parity form for the field I/O kernels.

@@ -93,6 +93,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   pf.band_lo = (float)pd.band_lo; pf.band_hi = (float)pd.band_hi;
   d.gamma_mode = p->gamma_mode;
   d.eos_fp64 = p->eos_fp64;
+  lbm::fill_slot_offsets(d, D);
 
   unsigned char* scratch = nullptr;
   lbm_status st = scratch_address(&scratch);

@@ -25,6 +25,19 @@ struct Ops {
 // Defined in lbm_d2q9.cu and lbm_d3q27.cu.
 extern const Ops ops_d2q9_fp64, ops_d2q9_fp32, ops_d3q27_fp64, ops_d3q27_fp32;
 
+// Fill the interior-node slot offset tables of d (needs d.N, d.nx, d.ny set).
+inline void fill_slot_offsets(DevDomain& d, int D) {
+  const int Q = D == 3 ? 27 : 9;
+  for (int i = 0; i < 27; ++i) {
+    const long long off = (long long)cxi(i) + (long long)d.nx * cyi(i) + (D == 3 ? (long long)d.nx * d.ny * czi(i) : 0ll);
+    const bool live = i < Q;
+    d.src_off[0][i] = live ? (long long)i * d.N : 0;
+    d.src_off[1][i] = live ? (long long)(Q - 1 - i) * d.N - off : 0;
+    d.dst_off[0][i] = live ? (long long)(Q - 1 - i) * d.N : 0;
+    d.dst_off[1][i] = live ? (long long)i * d.N + off : 0;
+  }
+}
+
 // Final fixed-order reduction of the diagnostic partial sums (lbm_d2q9.cu).
 void launch_diag_final(const double* partial, int nblocks, double* out, cudaStream_t s);
 

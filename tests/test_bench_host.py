@@ -1,0 +1,54 @@
+"""Host logic of bench.py for N > 1 ranks, on CPU with the gloo backend
+(world size 2): max-over-ranks timing, whole-job throughput, and the reference
+arm leaving every rank but 0 without work."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_ms = [12.5, 20.0][rank]
+    m = bench.max_over_ranks(local_ms, world)
+    bench.barrier(world)
+    q.put((rank, m, bench.whole_job_mlups(1000, 10, world, m)))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_weak_scaling_value_gloo():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    out = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, m, v in out:
+        assert m == 20.0  # the slowest rank's time, on every rank
+        assert v == pytest.approx(2 * 1000 * 10 / 20e-3 / 1e6)
+
+
+def test_reference_arm_only_rank0_works(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class Args:
+        gpus, steps, warmup, workload = 2, 1, 0, "drop3d"
+
+    assert bench.run_reference(Args()) == 0
+    assert capsys.readouterr().out == ""
