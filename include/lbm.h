@@ -50,7 +50,7 @@ typedef enum {
   LBM_ERR_OOM = 2,         /* device allocation failed */
   LBM_ERR_CUDA = 3,        /* a CUDA call failed */
   LBM_ERR_UNSTABLE = 4,    /* a non-finite or non-positive density appeared */
-  LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait (a shared-memory tile copy) gave up */
   LBM_ERR_STATE = 6        /* the handle is poisoned by an earlier error */
 } lbm_status;
 
@@ -203,9 +203,10 @@ const char* lbm_version(void);
  * The auxiliary fields between the two passes live in a 16 MiB scratch array
  * compiled into the library (every GPU that loads the library holds it until
  * the process exits).  Domains whose (2 + D) padded auxiliary fields,
- * (nx+4)(ny+4)(nz+4) values each in the storage type, need more than
- * 16 MiB - 256 B are rejected: for example 64x64x128 D3Q27 in float32 fits,
- * 128^3 does not; 1000x1000 D2Q9 in float32 fits.
+ * px(ny+4)(nz+4) values each in the storage type with px = nx+4 rounded up to
+ * a multiple of 4, need more than 16 MiB - 256 B are rejected: for example
+ * 64x64x128 D3Q27 in float32 fits, 128^3 does not; 1000x1000 D2Q9 in float32
+ * fits.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  Every call shares the one array: calls that overlap on

@@ -16,6 +16,7 @@ using lbm::Ops;
 using lbm::Phys;
 
 struct lbm_domain {
+  alignas(64) CUtensorMap aux_map;  // rho and s*psi halo tiles for the collide kernel's TMA load
   lbm_params p{};
   const Ops* ops = nullptr;
   DevDomain dev{};
@@ -102,7 +103,7 @@ Sizes sizes_of(const lbm_params& p, const Ops* ops) {
   s.D = p.lattice == LBM_D3Q27 ? 3 : 2;
   s.Q = s.D == 3 ? 27 : 9;
   s.N = (long long)p.nx * p.ny * (s.D == 3 ? p.nz : 1);
-  s.px = p.nx + 4;
+  s.px = lbm::padded_x(p.nx);
   s.py = p.ny + 4;
   s.pz = s.D == 3 ? p.nz + 4 : 1;
   s.PN = (long long)s.px * s.py * s.pz;
@@ -166,6 +167,13 @@ lbm_status drain_marks(lbm_domain* h) {
   return LBM_OK;
 }
 
+// Status for the device error word: bit 0 instability, bit 1 a bounded wait gave up.
+lbm_status flags_status(lbm_domain* h, unsigned int flags) {
+  if (flags & 2u) return fail(h, LBM_ERR_TIMEOUT, "a bounded device-side wait for a TMA tile gave up");
+  if (flags & 1u) return fail(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density in the domain");
+  return LBM_OK;
+}
+
 // Check the error flags copied by earlier steps without waiting for the GPU.
 lbm_status poll_flags(lbm_domain* h, bool wait) {
   if (!h->flags_pending) return LBM_OK;
@@ -177,8 +185,7 @@ lbm_status poll_flags(lbm_domain* h, bool wait) {
     if (q != cudaSuccess) return cuda_fail(h, q, "cudaEventQuery");
   }
   h->flags_pending = false;
-  if (*h->h_flags & 1u) return fail(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density in the domain");
-  return LBM_OK;
+  return flags_status(h, *h->h_flags);
 }
 
 lbm_status enqueue_flag_copy(lbm_domain* h) {
@@ -196,7 +203,7 @@ lbm_status launch_k(lbm_domain* h, int kind) {
     LBM_CUDA(h, cudaEventRecord(a, h->stream));
   }
   if (kind == 0) h->ops->moments_eos(h->dev, h->parity, h->stream);
-  else h->ops->collide_stream(h->dev, h->parity, h->stream);
+  else h->ops->collide_stream(h->dev, h->aux_map, h->parity, h->stream);
   h->launches += 1;
   LBM_CUDA(h, cudaGetLastError());
   if (h->timing) {
@@ -377,6 +384,14 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
   if ((err = cudaMemsetAsync(d.flags, 0, sizeof(unsigned int) + sizeof(unsigned long long) * 2, h->stream)) != cudaSuccess)
     return bail(err, "cudaMemset(flags)");
   if ((err = cudaMemsetAsync(d.aux, 0, s.aux_bytes, h->stream)) != cudaSuccess) return bail(err, "cudaMemset(aux)");
+  {
+    const char* why = nullptr;
+    if (!lbm::make_aux_map(&h->aux_map, d, s.D, h->ops->aux_bytes, &why)) {
+      g_create_error = why;
+      lbm_destroy(h);
+      return LBM_ERR_CUDA;
+    }
+  }
   if ((err = cudaMallocHost(&h->h_flags, sizeof(unsigned int))) != cudaSuccess) return bail(err, "cudaMallocHost");
   *h->h_flags = 0;
   if ((err = cudaEventCreateWithFlags(&h->flags_ev, cudaEventDisableTiming)) != cudaSuccess) return bail(err, "cudaEventCreate");
@@ -452,8 +467,7 @@ lbm_status lbm_synchronize(lbm_handle h) {
   if (st != LBM_OK) return st;
   // flags of the most recent steps
   LBM_CUDA(h, cudaMemcpy(h->h_flags, h->dev.flags, sizeof(unsigned int), cudaMemcpyDeviceToHost));
-  if (*h->h_flags & 1u) return fail(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density in the domain");
-  return LBM_OK;
+  return flags_status(h, *h->h_flags);
 }
 
 lbm_status lbm_read_macroscopic(lbm_handle h, double* rho, double* ux, double* uy, double* uz) {

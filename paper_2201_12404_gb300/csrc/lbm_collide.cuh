@@ -1,7 +1,9 @@
 // Pass 2 of a time step: force + collide + stream, one thread per interior node.
 //
-// A block owns a tile of Blocks<D> nodes and stages the density and the signed
-// pseudo-potential of the tile plus a 2-node halo in shared memory.  Each thread
+// A block owns a tile of Blocks<D> nodes.  One thread starts a TMA bulk-tensor
+// copy of the density and the signed pseudo-potential of the tile plus a 2-node
+// halo into shared memory; while it is in flight every thread gathers its
+// populations, then waits on the copy's mbarrier (bounded).  Each thread
 //   - gathers its Q pre-collision populations (A-A parity aware) into registers,
 //   - forms rho, j, Pi from row sums (the three populations sharing (cy, cz)),
 //   - evaluates the force of Eq. (Kforce_final) with the physical sign from the
@@ -17,6 +19,8 @@
 // offsets for the gather and the write; the others resolve wrap and walls.
 #pragma once
 
+#include <cuda.h>
+
 #include "lbm_device.cuh"
 
 // Minimum resident 256-thread blocks per SM requested from the register
@@ -27,6 +31,54 @@
 #define LBM_K2_MINBLOCKS(R) (sizeof(R) == 4 ? LBM_K2_MINBLOCKS_F32 : 1)
 
 namespace lbm {
+
+// ---- TMA and mbarrier helpers (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return done != 0;
+}
+
+// Wait for phase `parity` of the barrier, at most `limit` polls; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Tile copy of a D-dimensional halo box of the two staged fields (rank D + 1).
+template <int D>
+__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z) {
+  if (D == 3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
+        : "memory");
+  } else {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(0), "r"(smem_u32(bar))
+        : "memory");
+  }
+}
+
+// Polls of the tile barrier before a block reports a timeout (bit 1 of the
+// error word) and stops; far above any real copy latency.
+constexpr uint32_t kTileWaitPolls = 1u << 24;
 
 // Reciprocal for the entropic weights 1/f*_i: one MUFU approximation in float32
 // (relative error ~1 ulp, enough for sums that only set gamma), exact in float64.
@@ -68,15 +120,17 @@ constexpr size_t collide_dyn_smem() {
 
 template <int D, int P, typename S, typename R, typename A>
 __global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
-collide_stream_kernel(DevDomain d) {
+collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) {
   constexpr int Q = Lattice<D>::Q;
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
   constexpr int NT = BX * BY * BZ;
   constexpr int HX = BX + 4, HY = BY + 4, HZ = D == 3 ? BZ + 4 : 1;
   constexpr int HN = HX * HY * HZ;
   constexpr R cs2 = (R)(1.0 / 3.0);
-  __shared__ A s_rho[HN];
-  __shared__ A s_psi[HN];
+  __shared__ __align__(128) A s_aux[2 * HN];  // [field][z][y][x]: rho, then s*psi
+  __shared__ __align__(8) unsigned long long tile_bar;
+  const A* s_rho = s_aux;
+  const A* s_psi = s_aux + HN;
   // higher-order part h_i of every node of the tile, [i][thread] (dynamic: above 48 KB in float64)
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   R* s_h = (R*)smem_dyn;
@@ -85,33 +139,22 @@ collide_stream_kernel(DevDomain d) {
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
   const Phys<R>& ph = phys<R>(d);
 
-  // ---- stage rho and s*psi of the tile plus halo, one halo row (fixed y, z) per warp
-  //      at a time; padded coordinates start at the tile origin
-  {
-    const A* a_rho = (const A*)d.aux;
-    const A* a_psi = a_rho + d.PN;
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int r = warp; r < HY * HZ; r += NT / 32) {
-      const int yp = y0 + r % HY, zp = z0 + r / HY;
-      const bool row_ok = yp < d.py && zp < d.pz;
-      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
-#pragma unroll
-      for (int hx = lane; hx < HX; hx += 32) {
-        const bool ok = row_ok && x0 + hx < d.px;
-        s_rho[r * HX + hx] = ok ? a_rho[base + hx] : (A)1;
-        s_psi[r * HX + hx] = ok ? a_psi[base + hx] : (A)0;
-      }
-    }
-  }
+  // ---- start the halo-tile copy: padded coordinates of the tile's halo origin are
+  //      the tile origin itself; x0 is a multiple of 32, so the box starts 16-byte aligned
+  if (tid == 0) mbar_init(&tile_bar, 1);
   __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&tile_bar, (uint32_t)(2 * HN * sizeof(A)));
+    tma_load_tile<D>(s_aux, &aux_map, &tile_bar, x0, y0, z0);
+  }
 
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
-  if (x >= d.nx || y >= d.ny || z >= d.nz) return;
+  const bool active = x < d.nx && y < d.ny && z < d.nz;
   const long long n = node_of(d, x, y, z);
   const bool inner = interior<D>(d, x, y, z);
 
   R f[Q];
-  {
+  if (active) {
     const S* Fi = (const S*)d.f;
     if (inner) {
 #pragma unroll
@@ -121,6 +164,13 @@ collide_stream_kernel(DevDomain d) {
       for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(Fi + src_slot<D, P>(d, false, x, y, z, n, i));
     }
   }
+  // every thread waits, so that the block cannot retire while the copy is in flight
+  if (!mbar_wait_bounded(&tile_bar, 0, kTileWaitPolls)) {
+    if (tid == 0) atomicOr(d.flags, 2u);
+    mbar_wait_bounded(&tile_bar, 0, kTileWaitPolls);
+    return;
+  }
+  if (!active) return;
 
   // ---- rho, j, Pi from row sums: r0 = f- + f0 + f+, r1 = f+ - f-, r2 = f+ + f-
   R rho = 0, jx = 0, jy = 0, jz = 0, Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
@@ -138,11 +188,10 @@ collide_stream_kernel(DevDomain d) {
   const R u[3] = {jx * inv_rho, jy * inv_rho, jz * inv_rho};
 
   // ---- force: dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g, sums over the
-  //      lattice links row by row (rows rolled, the three x-links of a row unrolled)
-  //      with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz)
+  //      lattice links row by row with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz)
   const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
   R g4x = 0, g4y = 0, g4z = 0, g3x = 0, g3y = 0, g3z = 0;
-#pragma unroll 1
+#pragma unroll
   for (int row = 0; row < Q / 3; ++row) {
     const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
     const R wyz = (cy == 0 ? (R)2 : (R)0.5) * (D == 3 ? (cz == 0 ? (R)(2.0 / 3.0) : (R)(1.0 / 6.0)) : (R)1);

@@ -19,12 +19,12 @@ struct Launch {
     if (parity == 0) moments_eos_kernel<D, 0, S, R, A><<<grd, blk, 0, s>>>(d);
     else moments_eos_kernel<D, 1, S, R, A><<<grd, blk, 0, s>>>(d);
   }
-  static void collide_stream(const DevDomain& d, int parity, cudaStream_t s) {
+  static void collide_stream(const DevDomain& d, const CUtensorMap& map, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
     constexpr size_t smem = collide_dyn_smem<D, R>();
     auto k = parity == 0 ? collide_stream_kernel<D, 0, S, R, A> : collide_stream_kernel<D, 1, S, R, A>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<node_grid(d), blk, smem, s>>>(d);
+    k<<<node_grid(d), blk, smem, s>>>(d, map);
   }
   static unsigned blocks1d(const DevDomain& d) { return (unsigned)((d.N + 255) / 256); }
   static void init_equilibrium(const DevDomain& d, const double* rho, const double* ux, const double* uy,

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d) {
   const int xp = blockIdx.x * blockDim.x + threadIdx.x;
   const int yp = blockIdx.y * blockDim.y + threadIdx.y;
   const int zp = blockIdx.z * blockDim.z + threadIdx.z;
-  if (xp >= d.px || yp >= d.py || zp >= d.pz) return;
+  if (xp >= d.nx + 4 || yp >= d.py || zp >= d.pz) return;
   bool flip = false;
   auto image = [&](int c, int n, int wlo, int whi) {
     int t = c - 2;

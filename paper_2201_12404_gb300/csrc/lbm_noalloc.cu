@@ -57,7 +57,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   DevDomain d{};
   d.N = (long long)p->nx * p->ny * (D == 3 ? p->nz : 1);
   d.nx = p->nx; d.ny = p->ny; d.nz = D == 3 ? p->nz : 1;
-  d.px = p->nx + 4; d.py = p->ny + 4; d.pz = D == 3 ? p->nz + 4 : 1;
+  d.px = lbm::padded_x(p->nx); d.py = p->ny + 4; d.pz = D == 3 ? p->nz + 4 : 1;
   d.PN = (long long)d.px * d.py * d.pz;
   const double aux_bytes = (double)(2 + D) * (double)d.PN * (double)ops->aux_bytes;
   if (aux_bytes > (double)(kScratchBytes - kHeaderBytes)) return LBM_ERR_INVALID_ARG;  // beyond the scratch maximum
@@ -104,13 +104,17 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   d.aux = scratch + kHeaderBytes;
   d.gamma_out = nullptr;
 
+  alignas(64) CUtensorMap aux_map;
+  const char* why = nullptr;
+  if (!lbm::make_aux_map(&aux_map, d, D, ops->aux_bytes, &why)) return LBM_ERR_CUDA;
+
   cudaStream_t stream = (cudaStream_t)p->stream;
   // the scratch keeps the previous call's contents: clear the flags and the counter
   if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return LBM_ERR_CUDA;
   int parity = 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     ops->moments_eos(d, parity, stream);
-    ops->collide_stream(d, parity, stream);
+    ops->collide_stream(d, aux_map, parity, stream);
     parity ^= 1;
   }
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
