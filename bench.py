@@ -184,6 +184,20 @@ def run_reference(args):
     return 0
 
 
+def recorded_traffic(key):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None
+    when the kernel's source has changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[key]
+        h = hashlib.sha1()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["bytes_per_launch"] if h.hexdigest() == rec["source_sha1"] else None
+    except Exception:
+        return None
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -267,14 +281,7 @@ def run_ours(args):
     k1_ms = kms[0] / max(1, kcnt[0])
     k2_bytes = algorithmic_bytes_k2(wl, pop_bytes, pop_bytes)
     achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        t = prof.get("d3q27_fp32_collide_stream")
-        if t and t.get("kernel_rev") == "v1":
-            traffic = t["bytes_per_launch"]
-    except Exception:
-        pass
+    traffic = recorded_traffic("d3q27_fp32_collide_stream") if (args.precision == "fp32" and wl.N == 512 * 512 * 256) else None
     Q = 27
     line = {
         "metric": f"D3Q27 entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)",
