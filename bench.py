@@ -224,8 +224,8 @@ def run_ours(args):
     # a dedicated stream: the library launches on it and the timing events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    prec = lbm.LBM_FP64 if args.precision == "fp64" else lbm.LBM_FP32
-    pop_bytes = 8 if args.precision == "fp64" else 4
+    prec = {"fp64": lbm.LBM_FP64, "fp32": lbm.LBM_FP32, "fp16dev": lbm.LBM_FP16DEV}[args.precision]
+    pop_bytes = {"fp64": 8, "fp32": 4, "fp16dev": 2}[args.precision]
     p = WL.params(wl, prec, stream=stream.cuda_stream, rv=rv, rl=rl)
     rho0, u0 = WL.initial_fields(wl, rv, rl)
 
@@ -279,7 +279,9 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     k2_ms = kms[1] / max(1, kcnt[1])
     k1_ms = kms[0] / max(1, kcnt[0])
-    k2_bytes = algorithmic_bytes_k2(wl, pop_bytes, pop_bytes)
+    k2_bytes = algorithmic_bytes_k2(wl, pop_bytes, 8 if pop_bytes == 8 else 4)
+    if args.precision == "fp16dev":
+        k2_bytes += wl.N * 8  # writer densities: one read (the neighbours' are cache hits), one write
     achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
     traffic = recorded_traffic("d3q27_fp32_collide_stream") if (args.precision == "fp32" and wl.N == 512 * 512 * 256) else None
     Q = 27
@@ -287,7 +289,8 @@ def run_ours(args):
         "metric": f"D3Q27 entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)",
         "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if pop_bytes == 8 else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16dev": "f16 storage, f32 arithmetic"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": wl.name, "nodes": wl.N, "lattice": "D3Q27", "storage": f"{args.precision} A-A",
                    "l2": f"inputs larger than L2 ({27 * pop_bytes * wl.N / 1e9:.2f} GB populations), no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
@@ -319,7 +322,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp16dev"], default="fp32",
                     help="population storage/arithmetic of the timed path (fp32 is the headline)")
     ap.add_argument("--workload", default="drop3d", help="drop3d (default, 512x512x256) or drop3d-small "
                     "(256x256x128, the profiling case)")

@@ -61,8 +61,8 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q27 = 1 } lbm_lattice;
  * LBM_FP32: stored and computed in float32; float64 only in the Peng-Robinson
  *           pressure inside the interface band and in the gamma ratio.
  * LBM_FP16DEV: stored as float16 deviations f_i/(w_i rho_w) - 1, rho_w the
- *           density of the node that wrote the slot; computed in float32.
- *           (Not built yet: lbm_create_domain returns LBM_ERR_INVALID_ARG.) */
+ *           density of the node that wrote the slot (kept per node, one float32
+ *           per node and parity); computed in float32 like LBM_FP32. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2 } lbm_precision;
 
 /* Boundary of each face (-x,+x,-y,+y,-z,+z).  Periodic needs both faces of an
@@ -194,7 +194,8 @@ const char* lbm_version(void);
  *   p            domain parameters, validated as by lbm_create_domain; p->stream
  *                is the stream to run on (NULL = the legacy default stream).
  *   populations  device pointer to Q*N values of the storage type (float32 for
- *                LBM_FP32, float64 for LBM_FP64) in canonical order (see the
+ *                LBM_FP32, float64 for LBM_FP64; LBM_FP16DEV is not accepted
+ *                here) in canonical order (see the
  *                conventions above); read and overwritten in place.  The caller
  *                owns it.
  *   nsteps       even and >= 0, so that the state is in canonical order again on
@@ -212,8 +213,8 @@ const char* lbm_version(void);
  * any stream capture.  Every call shares the one array: calls that overlap on
  * the GPU (two streams, or two host threads) race and corrupt each other.
  * Asynchronous: returns once the work is enqueued.  No instability check.
- * Returns LBM_ERR_INVALID_ARG for NULL pointers, invalid parameters, odd or
- * negative nsteps, or a domain beyond the scratch maximum; LBM_ERR_CUDA if the
+ * Returns LBM_ERR_INVALID_ARG for NULL pointers, invalid parameters, LBM_FP16DEV,
+ * odd or negative nsteps, or a domain beyond the scratch maximum; LBM_ERR_CUDA if the
  * symbol lookup or a launch fails. */
 lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, int64_t nsteps);
 

@@ -45,7 +45,7 @@ static thread_local std::string g_create_error = "no error";
 
 namespace {
 
-const char* kVersion = "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP32, A-A streaming, sm_103a";
+const char* kVersion = "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP32/FP16-deviation, A-A streaming, sm_103a";
 
 bool is_wall(int v) { return v == LBM_BC_BOUNCEBACK; }
 
@@ -70,8 +70,8 @@ double pr_p(const EosCoeffs& e, double rho) {
 std::string validate(const lbm_params* p) {
   if (!p) return "params is NULL";
   if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q27) return "lattice must be LBM_D2Q9 or LBM_D3Q27";
-  if (p->precision == LBM_FP16DEV) return "LBM_FP16DEV storage is not available in this build";
-  if (p->precision != LBM_FP64 && p->precision != LBM_FP32) return "precision must be LBM_FP64 or LBM_FP32";
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32 && p->precision != LBM_FP16DEV)
+    return "precision must be LBM_FP64, LBM_FP32 or LBM_FP16DEV";
   const bool d3 = p->lattice == LBM_D3Q27;
   if (p->nx < 5 || p->ny < 5) return "nx and ny must be >= 5 (stencil radius 2)";
   if (d3 && p->nz < 5) return "nz must be >= 5 for D3Q27";
@@ -96,7 +96,7 @@ std::string validate(const lbm_params* p) {
   return "";
 }
 
-struct Sizes { int D, Q; long long N, PN; int px, py, pz; size_t f_bytes, aux_bytes, gamma_bytes; };
+struct Sizes { int D, Q; long long N, PN; int px, py, pz; size_t f_bytes, aux_bytes, gamma_bytes, rho_w_bytes; };
 
 Sizes sizes_of(const lbm_params& p, const Ops* ops) {
   Sizes s;
@@ -110,12 +110,16 @@ Sizes sizes_of(const lbm_params& p, const Ops* ops) {
   s.f_bytes = (size_t)s.Q * s.N * ops->pop_bytes;
   s.aux_bytes = (size_t)(2 + s.D) * s.PN * ops->aux_bytes;
   s.gamma_bytes = (size_t)s.N * sizeof(float);
+  s.rho_w_bytes = p.precision == LBM_FP16DEV ? 2 * (size_t)s.N * sizeof(float) : 0;
   return s;
 }
 
 const Ops* ops_for(const lbm_params& p) {
-  if (p.lattice == LBM_D2Q9) return p.precision == LBM_FP64 ? &lbm::ops_d2q9_fp64 : &lbm::ops_d2q9_fp32;
-  return p.precision == LBM_FP64 ? &lbm::ops_d3q27_fp64 : &lbm::ops_d3q27_fp32;
+  if (p.lattice == LBM_D2Q9)
+    return p.precision == LBM_FP64 ? &lbm::ops_d2q9_fp64
+                                   : (p.precision == LBM_FP16DEV ? &lbm::ops_d2q9_fp16dev : &lbm::ops_d2q9_fp32);
+  return p.precision == LBM_FP64 ? &lbm::ops_d3q27_fp64
+                                 : (p.precision == LBM_FP16DEV ? &lbm::ops_d3q27_fp16dev : &lbm::ops_d3q27_fp32);
 }
 
 lbm_status fail(lbm_domain* h, lbm_status st, const std::string& msg) {
@@ -273,7 +277,7 @@ lbm_status lbm_default_params(lbm_params* p) {
 size_t lbm_footprint_bytes(const lbm_params* p) {
   if (!validate(p).empty()) return 0;
   Sizes s = sizes_of(*p, ops_for(*p));
-  return s.f_bytes + s.aux_bytes + sizeof(unsigned int) + sizeof(unsigned long long);
+  return s.f_bytes + s.aux_bytes + s.rho_w_bytes + sizeof(unsigned int) + sizeof(unsigned long long);
 }
 
 lbm_status lbm_coexistence(const lbm_params* p, double* rho_vapour, double* rho_liquid, double* p_sat) {
@@ -378,6 +382,11 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
   }
   if ((err = cudaMalloc(&d.f, s.f_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(populations)");
   if ((err = cudaMalloc(&d.aux, s.aux_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(aux)");
+  if (s.rho_w_bytes) {
+    if ((err = cudaMalloc(&d.rho_w[0], s.rho_w_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(rho_w)");
+    d.rho_w[1] = d.rho_w[0] + s.N;
+    if ((err = cudaMemsetAsync(d.rho_w[0], 0, s.rho_w_bytes, h->stream)) != cudaSuccess) return bail(err, "cudaMemset(rho_w)");
+  }
   if ((err = cudaMalloc(&d.flags, sizeof(unsigned int) + sizeof(unsigned long long) * 2)) != cudaSuccess)
     return bail(err, "cudaMalloc(flags)");
   d.guards = (unsigned long long*)((char*)d.flags + sizeof(unsigned long long));
@@ -407,6 +416,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->dev.f) cudaFree(h->dev.f);
   if (h->dev.aux) cudaFree(h->dev.aux);
+  if (h->dev.rho_w[0]) cudaFree(h->dev.rho_w[0]);
   if (h->dev.flags) cudaFree(h->dev.flags);
   if (h->dev.gamma_out) cudaFree(h->dev.gamma_out);
   if (h->h_flags) cudaFreeHost(h->h_flags);

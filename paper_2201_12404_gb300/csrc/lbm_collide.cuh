@@ -154,16 +154,7 @@ collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) 
   const bool inner = interior<D>(d, x, y, z);
 
   R f[Q];
-  if (active) {
-    const S* Fi = (const S*)d.f;
-    if (inner) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(Fi + src_slot<D, P>(d, true, x, y, z, n, i));
-    } else {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(Fi + src_slot<D, P>(d, false, x, y, z, n, i));
-    }
-  }
+  if (active) gather<D, P, S, R>(d, x, y, z, f);
   // every thread waits, so that the block cannot retire while the copy is in flight
   if (!mbar_wait_bounded(&tile_bar, 0, kTileWaitPolls)) {
     if (tid == 0) atomicOr(d.flags, 2u);
@@ -331,6 +322,14 @@ collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) 
   const R ch = (R)0.5 * om * gamma;
 #pragma unroll
   for (int i = 0; i < Q; ++i) f[i] -= ch * s_h[i * NT + tid];
+
+  // ---- float16-deviation storage: encode against this node's density, which the
+  //      next step reads back as the writer density of every slot written here
+  if constexpr (DevStorage<S>::value) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = f[i] * (inv_rho * (R)(1.0 / wq<D>(i))) - (R)1;
+    d.rho_w[1 - P][n] = (float)rho;
+  }
 
   // ---- stream: A-A write
   S* Fo = (S*)d.f;

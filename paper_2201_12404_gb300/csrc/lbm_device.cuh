@@ -11,6 +11,7 @@
 // each odd step slot i of node r holds f_i(r) again.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,7 +68,19 @@ struct DevDomain {
   // src[0][i] = i N, src[1][i] = (Q-1-i) N - off(c_i); dst[0][i] = (Q-1-i) N,
   // dst[1][i] = i N + off(c_i), off(c) = cx + nx cy + nx ny cz.
   long long src_off[2][27], dst_off[2][27];
+  // Element offset of the upstream node r - c_i of an interior node: the node that
+  // wrote the slot population i of r is read from, in either parity.
+  long long up_off[27];
+  // float16-deviation storage only: density of the writer of every slot, by
+  // parity (a step of parity P decodes with rho_w[P] and records its own
+  // densities in rho_w[1 - P]); nullptr otherwise.
+  float* rho_w[2];
 };
+
+// float16-deviation storage: a slot holds delta = f/(w_i rho_w) - 1 in half
+// precision, rho_w being the density of the node that wrote it.
+template <typename S> struct DevStorage { static constexpr bool value = false; };
+template <> struct DevStorage<__half> { static constexpr bool value = true; };
 
 template <typename R> __device__ __forceinline__ const Phys<R>& phys(const DevDomain& d);
 template <> __device__ __forceinline__ const Phys<double>& phys<double>(const DevDomain& d) { return d.pd; }
@@ -76,6 +89,9 @@ template <> __device__ __forceinline__ const Phys<float>& phys<float>(const DevD
 // ---- storage conversion ----
 template <typename S, typename R> __device__ __forceinline__ R ld_pop(const S* p) { return (R)(*p); }
 template <typename S, typename R> __device__ __forceinline__ void st_pop(S* p, R v) { *p = (S)v; }
+template <> __device__ __forceinline__ float ld_pop<__half, float>(const __half* p) { return __half2float(*p); }
+template <> __device__ __forceinline__ double ld_pop<__half, double>(const __half* p) { return (double)__half2float(*p); }
+template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 
 __device__ __forceinline__ long long node_of(const DevDomain& d, int x, int y, int z) {
   return (long long)x + (long long)d.nx * ((long long)y + (long long)d.ny * (long long)z);
@@ -128,17 +144,45 @@ __device__ __forceinline__ long long dst_slot(const DevDomain& d, bool inner, in
   return wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz);
 }
 
+// Node that wrote the slot population i of node (x,y,z) is read from: the
+// upstream node r - c_i, or the node itself when that link crosses a wall.
+template <int D>
+__device__ __forceinline__ long long upstream_node(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
+  if (inner) return n + d.up_off[i];
+  bool wall = false;
+  const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
+  const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
+  const int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
+  return wall ? n : node_of(d, sx, sy, sz);
+}
+
 template <int D, int P, typename S, typename R>
 __device__ __forceinline__ void gather(const DevDomain& d, int x, int y, int z, R* f) {
   constexpr int Q = Lattice<D>::Q;
   const S* F = (const S*)d.f;
   const long long n = node_of(d, x, y, z);
-  if (interior<D>(d, x, y, z)) {
+  if constexpr (DevStorage<S>::value) {
+    // f_i = w_i rho_w (1 + delta_i)
+    const float* rw = d.rho_w[P];
+    if (interior<D>(d, x, y, z)) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, true, x, y, z, n, i));
+      for (int i = 0; i < Q; ++i)
+        f[i] = (R)wq<D>(i) * (R)rw[upstream_node<D>(d, true, x, y, z, n, i)] *
+               ((R)1 + ld_pop<S, R>(F + src_slot<D, P>(d, true, x, y, z, n, i)));
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        f[i] = (R)wq<D>(i) * (R)rw[upstream_node<D>(d, false, x, y, z, n, i)] *
+               ((R)1 + ld_pop<S, R>(F + src_slot<D, P>(d, false, x, y, z, n, i)));
+    }
   } else {
+    if (interior<D>(d, x, y, z)) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, false, x, y, z, n, i));
+      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, true, x, y, z, n, i));
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, false, x, y, z, n, i));
+    }
   }
 }
 

@@ -35,6 +35,7 @@ struct Launch {
     canonical_read_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, out);
   }
   static void canonical_write(const DevDomain& d, const double* in, cudaStream_t s) {
+    if constexpr (DevStorage<S>::value) canonical_density_kernel<D><<<blocks1d(d), 256, 0, s>>>(d, in);
     canonical_write_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, in);
   }
   static void macroscopic(const DevDomain& d, int parity, double* rho, double* u, cudaStream_t s) {

@@ -82,9 +82,23 @@ __global__ void init_equilibrium_kernel(DevDomain d, const double* rho, const do
     X[a][0] = a < D ? 0.5 * (1.0 / 3.0 + u2 - u[a]) : 0.0;
   }
   S* F = (S*)d.f;
+  if constexpr (DevStorage<S>::value) {
+    // each slot is encoded against the density of its upstream (writer) node; the
+    // next step (even parity) decodes with rho_w[0] of that node
+    const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+    const bool inner = interior<D>(d, x, y, z);
+    d.rho_w[0][n] = (float)r;
 #pragma unroll
-  for (int i = 0; i < Q; ++i)
-    st_pop<S, double>(F + (long long)i * d.N + n, r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1]);
+    for (int i = 0; i < Q; ++i) {
+      const double rw = (double)(float)rho[upstream_node<D>(d, inner, x, y, z, n, i)];
+      const double feq = r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1];
+      F[(long long)i * d.N + n] = __float2half_rn((float)(feq / (wq<D>(i) * rw) - 1.0));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      st_pop<S, double>(F + (long long)i * d.N + n, r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -107,7 +121,28 @@ __global__ void canonical_write_kernel(DevDomain d, const double* in) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.N) return;
   S* F = (S*)d.f;
-  for (int i = 0; i < Q; ++i) st_pop<S, double>(F + (long long)i * d.N + n, in[(long long)i * d.N + n]);
+  if constexpr (DevStorage<S>::value) {
+    // rho_w[0] holds every node's density (canonical_density_kernel, launched before)
+    const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+    const bool inner = interior<D>(d, x, y, z);
+    for (int i = 0; i < Q; ++i) {
+      const double rw = (double)d.rho_w[0][upstream_node<D>(d, inner, x, y, z, n, i)];
+      F[(long long)i * d.N + n] = __float2half_rn((float)(in[(long long)i * d.N + n] / (wq<D>(i) * rw) - 1.0));
+    }
+  } else {
+    for (int i = 0; i < Q; ++i) st_pop<S, double>(F + (long long)i * d.N + n, in[(long long)i * d.N + n]);
+  }
+}
+
+// float16-deviation storage: density of every node of a canonical state into rho_w[0].
+template <int D>
+__global__ void canonical_density_kernel(DevDomain d, const double* in) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  double r = 0.0;
+  for (int i = 0; i < Q; ++i) r += in[(long long)i * d.N + n];
+  d.rho_w[0][n] = (float)r;
 }
 
 // ---------------------------------------------------------------------------

@@ -50,6 +50,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   using lbm::Ops;
   if (!p || !populations || nsteps < 0 || (nsteps & 1)) return LBM_ERR_INVALID_ARG;
   if (lbm_footprint_bytes(p) == 0) return LBM_ERR_INVALID_ARG;  // same checks as lbm_create_domain
+  if (p->precision == LBM_FP16DEV) return LBM_ERR_INVALID_ARG;   // needs per-node writer densities
 
   const int D = p->lattice == LBM_D3Q27 ? 3 : 2;
   const Ops* ops = p->lattice == LBM_D2Q9 ? (p->precision == LBM_FP64 ? &lbm::ops_d2q9_fp64 : &lbm::ops_d2q9_fp32)

@@ -25,6 +25,7 @@ struct Ops {
 
 // Defined in lbm_d2q9.cu and lbm_d3q27.cu.
 extern const Ops ops_d2q9_fp64, ops_d2q9_fp32, ops_d3q27_fp64, ops_d3q27_fp32;
+extern const Ops ops_d2q9_fp16dev, ops_d3q27_fp16dev;
 
 // Fill the interior-node slot offset tables of d (needs d.N, d.nx, d.ny set).
 inline void fill_slot_offsets(DevDomain& d, int D) {
@@ -36,6 +37,7 @@ inline void fill_slot_offsets(DevDomain& d, int D) {
     d.src_off[1][i] = live ? (long long)(Q - 1 - i) * d.N - off : 0;
     d.dst_off[0][i] = live ? (long long)(Q - 1 - i) * d.N : 0;
     d.dst_off[1][i] = live ? (long long)i * d.N + off : 0;
+    d.up_off[i] = live ? -off : 0;
   }
 }
 

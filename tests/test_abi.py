@@ -87,6 +87,7 @@ def test_default_params_and_footprint(L):
     (dict(nz=3), "nz must be 1"),
     (dict(lattice=lbm.LBM_D3Q27, nz=4), "nz must be >= 5"),
     (dict(precision=7), "precision"),
+    (dict(precision=-1), "precision"),
     (dict(nu_liquid=0.0), "viscosities"),
     (dict(rho_vapour=2.0), "rho_liquid > rho_vapour"),
     (dict(bc=(1, 0, 0, 0, 0, 0)), "pairs"),

@@ -1,0 +1,131 @@
+"""GPU tests of the float16-deviation population storage (LBM_FP16DEV).
+
+A slot holds delta = f_i/(w_i rho_w) - 1 in half precision, rho_w being the
+density of the node that wrote it (the upstream node r - c_i of the population
+read at r, or r itself across a wall).  The expected stored state is built here
+on the host with numpy from the same definition (never from the CUDA path), and
+the FP64 oracle steps that decoded state.
+
+Tolerance.  Storing delta in half precision rounds it to 2^-11 relative; with
+|delta| <= ~0.2 in these states and a writer/reader density ratio up to ~3
+across a 5-node interface, one store costs up to ~3e-4 of w_i rho at the
+reading node; the float32 arithmetic adds ~2e-6.  A step is checked at 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from cases import case, drop_state, lbm_params, oracle_params, rel_err, shape
+from paper_2201_12404_gb300 import inputs as I
+from paper_2201_12404_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-3
+
+
+def upstream(c, D):
+    """Writer node index of every (population, node): r - c_i, or r across a wall."""
+    sh = shape(c)
+    nz, ny, nx = sh
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    vel = O.velocities(D)
+    walls = [(c["bc"][2 * a], c["bc"][2 * a + 1]) for a in range(3)]
+    out = np.zeros((len(vel),) + sh, dtype=np.int64)
+    for i, ci in enumerate(vel):
+        coords, wall = [], np.zeros(sh, bool)
+        for a, (g, n) in enumerate(((x, nx), (y, ny), (z, nz))):
+            if a >= D:
+                coords.append(g)
+                continue
+            t = g - ci[a]
+            lo, hi = walls[a]
+            wall |= (t < 0) & (lo == 1)
+            wall |= (t >= n) & (hi == 1)
+            coords.append(np.mod(t, n))
+        src = coords[0] + nx * (coords[1] + ny * coords[2])
+        own = x + nx * (y + ny * z)
+        out[i] = np.where(wall, own, src)
+    return out
+
+
+def host_codec(f, c):
+    """Encode canonical float64 populations as the library does on write, then decode."""
+    D = c["D"]
+    w = O.weights(D).reshape((-1, 1, 1, 1))
+    rho = f.sum(axis=0).astype(np.float32).astype(np.float64)
+    rw = rho.reshape(-1)[upstream(c, D)]
+    delta = (f / (w * rw) - 1.0).astype(np.float32).astype(np.float16)  # as the library: float64 -> float32 -> half
+    return w * rw * (1.0 + delta.astype(np.float64))
+
+
+CASES = {
+    "d2q9_walls": dict(D=2, nx=67, ny=29, walls=True),
+    "d3q27_walls": dict(D=3, nx=35, ny=9, nz=12, walls=True),
+    "d3q27_periodic": dict(D=3, nx=37, ny=13, nz=11),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_write_read_is_the_host_codec(name):
+    c = case(**CASES[name], precision=lbm.LBM_FP16DEV)
+    f0 = drop_state(c)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(f0)
+        back = dom.lbm_read_populations()
+    expect = host_codec(f0, c)
+    assert rel_err(back, expect, c["D"]).max() < 2e-6
+    # and the codec itself is within half precision of the input
+    assert rel_err(expect, f0, c["D"]).max() < 2e-3
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_matches_oracle(name):
+    c = case(**CASES[name], precision=lbm.LBM_FP16DEV)
+    f0 = drop_state(c)
+    start = host_codec(f0, c)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(f0)
+        dom.lbm_step(1)
+        fg = dom.lbm_read_populations()
+    fo, _ = O.run(oracle_params(c), start, 1)
+    e = rel_err(fg, fo, c["D"]).max()
+    assert e <= TOL_STEP, e
+
+
+def test_three_steps_match_oracle():
+    c = case(**CASES["d3q27_walls"], precision=lbm.LBM_FP16DEV)
+    f0 = drop_state(c)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(f0)
+        dom.lbm_step(3)
+        fg = dom.lbm_read_populations()
+    fo, _ = O.run(oracle_params(c), host_codec(f0, c), 3)
+    assert rel_err(fg, fo, 3).max() <= 3 * TOL_STEP
+
+
+def test_init_fields_encodes_equilibrium():
+    c = case(3, 20, 11, 9, precision=lbm.LBM_FP16DEV)
+    sh = shape(c)
+    rho = I.drop(sh, (10, 5, 4), 4, c["rho_l"], c["rho_v"], 4.0, D=3)
+    u = I.rng(3).uniform(-0.03, 0.03, (3,) + sh)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_init_fields(rho, u)
+        fg = dom.lbm_read_populations()
+    fo = O.init_equilibrium(oracle_params(c), rho, u)
+    assert rel_err(fg, fo, 3).max() < 2e-3
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_mass_drift_is_bounded(D):
+    dims = dict(nx=64, ny=48) if D == 2 else dict(nx=24, ny=20, nz=16)
+    c = case(D, **dims, precision=lbm.LBM_FP16DEV)
+    f0 = drop_state(c, perturb=0.0)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(f0)
+        m0 = dom.lbm_read_diag()["mass"]
+        dom.lbm_step(100)
+        m1 = dom.lbm_read_diag()["mass"]
+    # half-precision rounding of every stored deviation is unbiased: the drift is a
+    # random walk far below one ulp of a single population per step
+    assert abs(m1 - m0) <= 1e-4 * m0
