@@ -149,7 +149,7 @@ def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
     p = O.make_params(wl.D, nx, ny, nz, T_over_Tc=wl.T_over_Tc, kappa=wl.kappa, nu_liquid=nu_l,
                       nu_vapour=nu_v, rho_liquid=rl, rho_vapour=rv, bc=bc, **WL.PAPER_EOS)
     rho, u = WL.initial_fields(wl, rv, rl, crop=crop)
-    f = O.init_equilibrium(p, rho, u)
+    f = O.init_physical(p, rho, u)
     t0 = time.perf_counter()
     O.run(p, f, steps)
     dt = time.perf_counter() - t0

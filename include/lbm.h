@@ -111,9 +111,14 @@ lbm_status lbm_default_params(lbm_params* p);
  * lbm_last_error(NULL)), OOM, CUDA. */
 lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out);
 
-/* f := f^eq(rho, u) (Eq. LBMeq) at every node from host arrays of N values
- * each (uz is NULL in 2-D).  u is the bare velocity sum_i c_i f_i / rho.
- * Resets the step counter and the streaming parity.  Synchronising. */
+/* Initial state from host arrays of N values each (uz is NULL in 2-D): the
+ * equilibrium f^eq(rho, u_b) of Eq. (LBMeq) at the bare velocity
+ * u_b = u - F dt/(2 rho), F the force of the density field rho (Eq.
+ * Kforce_final plus rho g), so that the reported velocity of the initial state
+ * (see lbm_read_macroscopic) is u.  Starting from u_b = u instead leaves an
+ * impulse of F/(2 rho) at every interface, which destabilises runs at large
+ * density ratios.  Resets the step counter and the streaming parity.
+ * Synchronising. */
 lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, const double* uy,
                            const double* uz);
 

@@ -107,6 +107,7 @@ def lib():
                 "orc_force": (None, [P, _dp, _dp, _dp]),
                 "orc_phi": (None, [P, _dp, _dp, _dp]),
                 "orc_init_equilibrium": (None, [P, _dp, _dp, _dp]),
+                "orc_init_physical": (None, [P, _dp, _dp, _dp]),
                 "orc_macroscopic": (None, [P, _dp, _dp, _dp]),
                 "orc_step": (ctypes.c_long, [P, _dp, _dp, ctypes.c_void_p]),
                 "orc_run": (ctypes.c_long, [P, _dp, ctypes.c_long]),
@@ -256,6 +257,13 @@ def phi(p: Params, rho, q):
 def init_equilibrium(p: Params, rho0, u0):
     f = np.zeros((Q_of(p.D),) + _shape(p))
     lib().orc_init_equilibrium(ctypes.byref(p), _f64(rho0), _f64(u0), f)
+    return f
+
+
+def init_physical(p: Params, rho0, u0):
+    """Equilibrium whose reported velocity u + F/(2 rho) is u0 (the library's lbm_init_fields)."""
+    f = np.zeros((Q_of(p.D),) + _shape(p))
+    lib().orc_init_physical(ctypes.byref(p), _f64(rho0), _f64(u0), f)
     return f
 
 

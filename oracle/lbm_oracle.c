@@ -25,6 +25,8 @@
  *  - walls: half-way bounce-back; auxiliary ghosts mirrored, q negated.
  *  - gamma guards: any f*_i <= 0 -> gamma = 2 at that node; <dh|dh> <= 1e-300
  *    -> ratio 0.  No clipping.
+ *  - initial state: equilibrium at the bare velocity u0 - F dt/(2 rho0), so that
+ *    the reported (exact-difference-method) velocity starts at u0.
  *  - D3Q27 moment set: the 27 tensor products H_p(x)H_q(y)H_r(z), p,q,r<=2,
  *    with the three diagonal second-order moments recombined into two
  *    differences and the trace (the printed list repeats a_{x^2y^2} where
@@ -454,6 +456,27 @@ void orc_init_equilibrium(const orc_params* p, const double* rho0, const double*
     orc_feq(D, rho0[n], u, feq);
     for (int i = 0; i < Q; ++i) f[i * N + n] = feq[i];
   }
+}
+
+/* Start at rest in the reported sense: f = f^eq(rho0, u0 - F(rho0) dt/(2 rho0)), F the
+ * force of the initial density field (pseudo-potential and capillary terms plus rho g),
+ * so that the reported velocity u + F dt/(2 rho) of the initial state is u0. */
+void orc_init_physical(const orc_params* p, const double* rho0, const double* u0 /* D*N */, double* f) {
+  int D = p->D;
+  long N = n_nodes(p);
+  double* spsi = malloc(sizeof(double) * N);
+  double* F = malloc(sizeof(double) * D * N);
+  double* ub = malloc(sizeof(double) * D * N);
+  for (long n = 0; n < N; ++n) {
+    double sg;
+    double ps = orc_psi(p, rho0[n], &sg);
+    spsi[n] = sg * ps;
+  }
+  orc_force(p, rho0, spsi, F);
+  for (int al = 0; al < D; ++al)
+    for (long n = 0; n < N; ++n) ub[al * N + n] = u0[al * N + n] - F[al * N + n] / (2.0 * rho0[n]);
+  orc_init_equilibrium(p, rho0, ub, f);
+  free(spsi); free(F); free(ub);
 }
 
 /* Reported velocity: u + F dt / (2 rho) (exact-difference-method convention). */

@@ -437,12 +437,18 @@ lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, co
   LBM_CUDA(h, cudaMemcpyAsync(buf + h->dev.N, ux, nb, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(h, cudaMemcpyAsync(buf + 2 * h->dev.N, uy, nb, cudaMemcpyHostToDevice, h->stream));
   if (D == 3) LBM_CUDA(h, cudaMemcpyAsync(buf + 3 * h->dev.N, uz, nb, cudaMemcpyHostToDevice, h->stream));
-  h->ops->init_equilibrium(h->dev, buf, buf + h->dev.N, buf + 2 * h->dev.N, D == 3 ? buf + 3 * h->dev.N : nullptr, h->stream);
-  h->launches += 1;
+  double* uz_d = D == 3 ? buf + 3 * h->dev.N : nullptr;
+  // equilibrium at the requested velocity, its auxiliary fields, then the bare velocity
+  // u - F/(2 rho) and the equilibrium there, so that the reported velocity is u
+  h->ops->init_equilibrium(h->dev, buf, buf + h->dev.N, buf + 2 * h->dev.N, uz_d, h->stream);
+  h->parity = 0;
+  h->ops->moments_eos(h->dev, 0, h->stream);
+  h->ops->bare_velocity(h->dev, buf, buf + h->dev.N, h->stream);
+  h->ops->init_equilibrium(h->dev, buf, buf + h->dev.N, buf + 2 * h->dev.N, uz_d, h->stream);
+  h->launches += 4;
   LBM_CUDA(h, cudaGetLastError());
   LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-  h->parity = 0;
   h->steps = 0;
   return LBM_OK;
 }

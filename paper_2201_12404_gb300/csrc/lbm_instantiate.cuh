@@ -41,13 +41,16 @@ struct Launch {
   static void macroscopic(const DevDomain& d, int parity, double* rho, double* u, cudaStream_t s) {
     macroscopic_kernel<D, S, R, A><<<blocks1d(d), 256, 0, s>>>(d, parity, rho, u);
   }
+  static void bare_velocity(const DevDomain& d, const double* rho, double* u, cudaStream_t s) {
+    bare_velocity_kernel<D, R, A><<<blocks1d(d), 256, 0, s>>>(d, rho, u);
+  }
   static int diag_partial(const DevDomain& d, int parity, double* partial, cudaStream_t s) {
     diag_partial_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, partial);
     return (int)blocks1d(d);
   }
   static Ops table() {
     return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
-               &canonical_read, &canonical_write, &macroscopic, &diag_partial};
+               &canonical_read, &canonical_write, &macroscopic, &bare_velocity, &diag_partial};
   }
 };
 

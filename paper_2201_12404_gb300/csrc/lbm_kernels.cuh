@@ -184,6 +184,40 @@ __global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, dou
 }
 
 // ---------------------------------------------------------------------------
+// Bare velocity of a state at rest in the reported sense: u -= F dt/(2 rho) in
+// place, F from the auxiliary fields of the current (equilibrium) state.
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename A>
+__global__ void bare_velocity_kernel(DevDomain d, const double* rho_in, double* u) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+  const A* a_rho = (const A*)d.aux;
+  const A* a_psi = a_rho + d.PN;
+  const long long pc = pnode_of<D>(d, x, y, z);
+  const long long sy = d.px, sz = (long long)d.px * d.py;
+  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
+  for (int i = 0; i < Q; ++i) {
+    if (i == Lattice<D>::REST) continue;
+    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
+    const R t4 = (R)(4.0 / 3.0) * fabs((R)a_psi[pc + o]) - (R)(1.0 / 6.0) * fabs((R)a_psi[pc + 2 * o]);
+    const R t3 = (R)2 * (R)a_rho[pc + o] - (R)a_rho[pc + 2 * o];
+    const R W = (R)(3.0 * wq<D>(i));
+    for (int a = 0; a < D; ++a) {
+      const int c = cq<D>(i, a);
+      g4[a] += W * (R)c * t4;
+      g3[a] += W * (R)c * t3;
+    }
+  }
+  const R rho = (R)a_rho[pc];
+  for (int a = 0; a < D; ++a) {
+    const R Fa = -((R)2 * (R)a_psi[pc] * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
+    u[a * d.N + n] -= (double)Fa / (2.0 * rho_in[n]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic totals: per-block partial sums (fixed order), then one block.
 // partial layout: [block][5] = mass, jx, jy, jz, max|u|.
 // ---------------------------------------------------------------------------

@@ -19,6 +19,8 @@ struct Ops {
   void (*canonical_read)(const DevDomain&, int parity, double* out, cudaStream_t);
   void (*canonical_write)(const DevDomain&, const double* in, cudaStream_t);
   void (*macroscopic)(const DevDomain&, int parity, double* rho, double* u, cudaStream_t);
+  // u[a*N + n] -= F_a/(2 rho[n]), F from the current auxiliary fields
+  void (*bare_velocity)(const DevDomain&, const double* rho, double* u, cudaStream_t);
   // returns the number of partial blocks written to partial (5 doubles each)
   int (*diag_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
 };

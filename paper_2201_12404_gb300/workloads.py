@@ -49,13 +49,13 @@ class Workload:
 # D3Q27 drop impact on a thin film, 512x512x256, density ratio ~1000 (T/Tc = 0.59)
 DROP_IMPACT_3D = Workload(
     name="D3Q27 drop impact on a thin film 512x512x256 (rho_l/rho_v ~ 1000, R = 64, U = 0.04, h = 0.2R)",
-    D=3, nx=512, ny=512, nz=256, T_over_Tc=0.59, kappa=0.005, nu_liquid=0.005, mu_ratio=50.0,
+    D=3, nx=512, ny=512, nz=256, T_over_Tc=0.59, kappa=0.01, nu_liquid=0.005, mu_ratio=50.0,
     R=64.0, U=0.04, film=0.2, steps=5000, walls_axis=2)
 
 # D2Q9 drop impact, 2048x1024, Re ~ 2000, We ~ 250
 DROP_IMPACT_2D = Workload(
     name="D2Q9 drop impact on a thin film 2048x1024 (rho_l/rho_v ~ 1000, R = 128, U = 0.05, h = 0.2R)",
-    D=2, nx=2048, ny=1024, nz=1, T_over_Tc=0.59, kappa=0.005, nu_liquid=0.0064, mu_ratio=50.0,
+    D=2, nx=2048, ny=1024, nz=1, T_over_Tc=0.59, kappa=0.01, nu_liquid=0.0064, mu_ratio=50.0,
     R=128.0, U=0.05, film=0.2, steps=20000, walls_axis=1)
 
 # D2Q9 static drop, 128x128 periodic, T/Tc = 0.8
@@ -69,7 +69,7 @@ STATIC_DROP_2D = Workload(
 # populations: still far larger than L2), the case kernel profiles are taken on.
 DROP_IMPACT_3D_SMALL = Workload(
     name="D3Q27 drop impact on a thin film 256x256x128 (rho_l/rho_v ~ 1000, R = 32, U = 0.04, h = 0.2R)",
-    D=3, nx=256, ny=256, nz=128, T_over_Tc=0.59, kappa=0.005, nu_liquid=0.005, mu_ratio=50.0,
+    D=3, nx=256, ny=256, nz=128, T_over_Tc=0.59, kappa=0.01, nu_liquid=0.005, mu_ratio=50.0,
     R=32.0, U=0.04, film=0.2, steps=5000, walls_axis=2)
 
 WORKLOADS = {"drop3d": DROP_IMPACT_3D, "drop3d-small": DROP_IMPACT_3D_SMALL, "drop2d": DROP_IMPACT_2D,

@@ -112,7 +112,7 @@ def test_init_fields_encodes_equilibrium():
     with lbm.Domain(lbm_params(c)) as dom:
         dom.lbm_init_fields(rho, u)
         fg = dom.lbm_read_populations()
-    fo = O.init_equilibrium(oracle_params(c), rho, u)
+    fo = O.init_physical(oracle_params(c), rho, u)
     assert rel_err(fg, fo, 3).max() < 2e-3
 
 

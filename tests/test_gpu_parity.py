@@ -116,7 +116,7 @@ def test_macroscopic_matches_oracle():
         assert np.max(np.abs(u_g - u_o)) < 1e-13
 
 
-def test_init_fields_is_equilibrium_of_oracle():
+def test_init_fields_matches_oracle_and_reports_the_requested_velocity():
     c = case(3, 20, 11, 9)
     sh = shape(c)
     rho = I.drop(sh, (10, 5, 4), 4, c["rho_l"], c["rho_v"], 4.0, D=3)
@@ -124,8 +124,10 @@ def test_init_fields_is_equilibrium_of_oracle():
     with lbm.Domain(lbm_params(c)) as dom:
         dom.lbm_init_fields(rho, u)
         fg = dom.lbm_read_populations()
-    fo = O.init_equilibrium(oracle_params(c), rho, u)
-    assert rel_err(fg, fo, 3).max() < 1e-15
+        _, ug = dom.lbm_read_macroscopic()
+    fo = O.init_physical(oracle_params(c), rho, u)
+    assert rel_err(fg, fo, 3).max() < 1e-14
+    assert np.max(np.abs(ug - u)) < 1e-13
 
 
 def test_write_read_roundtrip_and_step_zero():

@@ -496,3 +496,22 @@ def test_flat_interface_coexistence_tracks_maxwell():
     r, _ = O.macroscopic(p, f)
     assert r[0, 2, 60] == pytest.approx(rl, rel=1e-2)
     assert r[0, 2, 0] == pytest.approx(rv, rel=6e-2)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_physical_initial_state_reports_the_requested_velocity(D):
+    """Initial state at rest in the reported sense: its exact-difference-method velocity
+    u + F/(2 rho) is the requested u0, and it is an equilibrium (f = f^eq(rho0, u_bare))."""
+    n = 16 if D == 2 else 10
+    p, _ = _two_phase_drop(D, n)
+    shape = (n if D == 3 else 1, n, n)
+    rho = I.drop(shape, (n / 2, n / 2, n / 2), n / 4, p.rho_liquid, p.rho_vapour, 4.0, D=D)
+    u0 = I.rng(12).uniform(-0.01, 0.01, (D,) + shape)
+    f = O.init_physical(p, rho, u0)
+    r, u = O.macroscopic(p, f)
+    assert np.max(np.abs(r - rho)) < 1e-13 * rho.max()
+    assert np.max(np.abs(u - u0)) < 1e-14
+    # the force field is not zero there, so the bare velocity differs from u0
+    c = O.velocities(D).astype(float)
+    ub = np.einsum("ia,i...->a...", c[:, :D], f) / r
+    assert np.max(np.abs(ub - u0)) > 1e-4
