@@ -186,6 +186,51 @@ int64_t lbm_launch_count(lbm_handle h);
  * lbm_coexistence on this thread when h is NULL.  Never NULL. */
 const char* lbm_last_error(lbm_handle h);
 
+/* ---- Batches: many D2Q9 domains advanced by one persistent launch ----
+ *
+ * A batch holds D2Q9 domains of one precision and any sizes and parameters.
+ * lbm_batch_step advances all of them by nsteps time steps with a single
+ * cooperative (all blocks resident) kernel launch: the blocks walk a work list of
+ * (domain, tile) items for pass 1, meet at a grid barrier, walk the pass-2 items,
+ * and repeat per step.  Every grid-barrier wait is bounded; a wait that gives up
+ * stops the kernel and surfaces as LBM_ERR_TIMEOUT.  The launch is captured in a
+ * CUDA graph per distinct nsteps (replayed afterwards) when the driver accepts
+ * capturing a cooperative launch, and launched directly otherwise.  Work runs on
+ * the stream of the first domain.  While a domain belongs to a batch, advance it
+ * only through the batch.  The results are the same as stepping each domain alone
+ * (same kernels' per-tile arithmetic). */
+typedef struct lbm_batch* lbm_batch_handle;
+
+/* Create a batch over `count` >= 1 distinct domains (the caller keeps owning
+ * them; destroy the batch before them).  Synchronising. */
+lbm_status lbm_batch_create(const lbm_handle* domains, int32_t count, lbm_batch_handle* out);
+
+/* Advance every domain of the batch by nsteps >= 0 time steps (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch_handle b, int64_t nsteps);
+
+/* Wait for the batch; LBM_ERR_TIMEOUT if a grid-barrier wait gave up, otherwise the
+ * first error of lbm_synchronize over the domains.  Synchronising. */
+lbm_status lbm_batch_synchronize(lbm_batch_handle b);
+
+/* Tile-shape autotuner: time every compiled tile shape of the persistent kernel for
+ * trial_steps steps on copies of the batch's domains (the domains themselves do not
+ * advance) and keep the fastest.  cache_path (nullable) names a file of JSON lines
+ * {"key": ..., "block": [bx, by], "ms_per_step": ...}; a line whose key matches this
+ * batch's size class (precision, total nodes rounded down to a power of two, domain
+ * count) is used without timing, and a new choice is appended.  Synchronising. */
+lbm_status lbm_batch_tune(lbm_batch_handle b, int32_t trial_steps, const char* cache_path);
+
+/* Chosen tile shape, grid size (blocks) and whether launches go through a CUDA graph. */
+lbm_status lbm_batch_info(lbm_batch_handle b, int32_t* block_x, int32_t* block_y, int32_t* grid_blocks,
+                          int32_t* graph_captured);
+
+/* Release the batch (not its domains).  NULL-safe. */
+lbm_status lbm_batch_destroy(lbm_batch_handle b);
+
+/* Message of the last error on b, or of the last failed lbm_batch_create on this
+ * thread when b is NULL. */
+const char* lbm_batch_last_error(lbm_batch_handle b);
+
 /* Library build string (lattices, precisions, target architecture). */
 const char* lbm_version(void);
 

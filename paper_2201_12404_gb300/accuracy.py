@@ -6,9 +6,11 @@ with the float64 one:
 
   - density L_inf error relative to the liquid density,
   - velocity L_inf error relative to max |u| of the float64 field,
+  - the same two errors averaged over the domain (a moving interface shifted by
+    one node already gives an L_inf density error of order one),
   - spreading radius of the drop-impact workloads: the largest horizontal
     distance from the impact axis of a node with rho > (rho_l + rho_v)/2 in the
-    layer two nodes above the initial film (Secs. 3.2-3.3),
+    layer two nodes above the initial film (Secs. 3.2-3.3), at several times,
   - mass drift of every path.
 
 The static drop (Sec. 3.1.2) also reports the Laplace pressure jump
@@ -49,53 +51,70 @@ def spreading_radius(rho, wl: WL.Workload, rv, rl):
     return float(np.max(np.hypot(xs - 0.5 * (wl.nx - 1), ys - 0.5 * (wl.ny - 1))))
 
 
-def run_path(wl, precision, rho0, u0, steps, rv, rl):
-    p = WL.params(wl, precision, rv=rv, rl=rl)
-    with lbm.Domain(p) as dom:
-        dom.lbm_init_fields(rho0, u0)
-        m0 = dom.lbm_read_diag()["mass"]
-        t0 = time.perf_counter()
-        status = "ok"
-        try:
-            dom.lbm_step(steps)
-            dom.lbm_synchronize()
-        except lbm.LBMError as e:
-            status = str(e)
-        dt = time.perf_counter() - t0
-        if status != "ok":
-            return dict(status=status, seconds=dt)
-        rho, u = dom.lbm_read_macroscopic()
-        m1 = dom.lbm_read_diag()["mass"]
-    return dict(status=status, seconds=dt, rho=rho, u=u, mass_drift=(m1 - m0) / m0)
-
-
-def compare(wl, steps, quick=False):
+def compare(wl, checkpoints):
+    """The three paths advanced in lockstep from the same initial fields; at every
+    checkpoint the float32 and float16-deviation fields are compared with float64."""
     rv, rl = WL.coexistence(wl)
     rho0, u0 = WL.initial_fields(wl, rv, rl)
-    out = dict(workload=wl.name, steps=steps, rho_liquid=rl, rho_vapour=rv)
-    ref = None
-    for name, prec in (("fp64", lbm.LBM_FP64), ("fp32", lbm.LBM_FP32), ("fp16dev", lbm.LBM_FP16DEV)):
-        r = run_path(wl, prec, rho0, u0, steps, rv, rl)
-        entry = dict(status=r["status"], seconds=round(r["seconds"], 3),
-                     mlups=wl.N * steps / r["seconds"] / 1e6 if r["status"] == "ok" else None)
-        if r["status"] == "ok":
-            entry["mass_drift"] = r["mass_drift"]
-            if wl.U > 0:
-                entry["spreading_radius"] = spreading_radius(r["rho"], wl, rv, rl)
-            if name == "fp64":
-                ref = r
-            elif ref is not None:
-                umax = float(np.max(np.abs(ref["u"])))
-                entry["rho_linf_rel"] = float(np.max(np.abs(r["rho"] - ref["rho"])) / rl)
-                entry["u_linf_rel"] = float(np.max(np.abs(r["u"] - ref["u"])) / max(umax, 1e-300))
-                if "spreading_radius" in entry:
-                    entry["spreading_radius_diff"] = entry["spreading_radius"] - out["fp64"].get("spreading_radius", 0.0)
-        out[name] = entry
+    names = (("fp64", lbm.LBM_FP64), ("fp32", lbm.LBM_FP32), ("fp16dev", lbm.LBM_FP16DEV))
+    doms = {}
+    out = dict(workload=wl.name, rho_liquid=rl, rho_vapour=rv, tau_steps=(2 * wl.R / wl.U if wl.U > 0 else None),
+               checkpoints=[])
+    try:
+        for name, prec in names:
+            doms[name] = lbm.Domain(WL.params(wl, prec, rv=rv, rl=rl))
+            doms[name].lbm_init_fields(rho0, u0)
+        mass0 = {k: d.lbm_read_diag()["mass"] for k, d in doms.items()}
+        seconds = {k: 0.0 for k in doms}
+        failed = {}
+        done = 0
+        for cp in checkpoints:
+            snap = {}
+            for k, d in doms.items():
+                if k in failed:
+                    continue
+                t0 = time.perf_counter()
+                try:
+                    d.lbm_step(cp - done)
+                    d.lbm_synchronize()
+                except lbm.LBMError as e:
+                    failed[k] = f"{e} (before step {cp})"
+                    continue
+                seconds[k] += time.perf_counter() - t0
+                rho, u = d.lbm_read_macroscopic()
+                snap[k] = dict(rho=rho, u=u, mass_drift=(d.lbm_read_diag()["mass"] - mass0[k]) / mass0[k])
+            done = cp
+            row = dict(step=cp)
+            ref = snap.get("fp64")
+            for k in doms:
+                if k not in snap:
+                    row[k] = dict(status=failed.get(k, "failed"))
+                    continue
+                e = dict(mass_drift=snap[k]["mass_drift"])
+                if wl.U > 0:
+                    e["spreading_radius"] = spreading_radius(snap[k]["rho"], wl, rv, rl)
+                if k != "fp64" and ref is not None:
+                    dr = np.abs(snap[k]["rho"] - ref["rho"]) / rl
+                    umax = max(float(np.max(np.abs(ref["u"]))), 1e-300)
+                    du = np.abs(snap[k]["u"] - ref["u"]) / umax
+                    e.update(rho_linf_rel=float(dr.max()), rho_l1_rel=float(dr.mean()),
+                             u_linf_rel=float(du.max()), u_l1_rel=float(du.mean()))
+                    if "spreading_radius" in e:
+                        e["spreading_radius_diff"] = e["spreading_radius"] - spreading_radius(ref["rho"], wl, rv, rl)
+                row[k] = e
+            out["checkpoints"].append(row)
+        out["mlups"] = {k: (wl.N * done / seconds[k] / 1e6 if k not in failed and seconds[k] > 0 else None)
+                        for k in doms}
+    finally:
+        for d in doms.values():
+            d.close()
     return out
 
 
 def laplace(wl_base, radii, steps):
-    """Static drops of two radii (float64): Delta P R_e for each."""
+    """Static drops (float64): Delta P and the equimolar radius R_e for each initial radius.
+    Densities inside/outside are averages over the drop core (r < R_e/2) and over the
+    far field (r > R_e + 12); Delta P uses the Peng-Robinson pressure of those densities."""
     from . import inputs as I
     rv, rl = WL.coexistence(wl_base)
     res = []
@@ -110,16 +129,17 @@ def laplace(wl_base, radii, steps):
             dom.lbm_step(steps)
             rho, u = dom.lbm_read_macroscopic()
             m1 = dom.lbm_read_diag()["mass"]
-        c = (sh[1] // 2, sh[2] // 2)
-        r_in = float(rho[0, c[0], c[1]])
-        r_out = float(rho[0, 0, 0])
-        # equimolar radius of a 2-D drop: area of the excess mass over the jump
+        yy, xx = np.meshgrid(np.arange(sh[1]), np.arange(sh[2]), indexing="ij")
+        r = np.hypot(xx - sh[2] / 2, yy - sh[1] / 2)
+        r_out = float(np.mean(rho[0][r > R + 12]))
+        r_in0 = float(np.mean(rho[0][r < R / 2]))
+        # equimolar radius of a 2-D drop: the disc holding the excess mass at the bulk jump
         excess = float(np.sum(rho - r_out))
-        Re = math.sqrt(excess / (math.pi * (r_in - r_out)))
+        Re = math.sqrt(excess / (math.pi * (r_in0 - r_out)))
+        r_in = float(np.mean(rho[0][r < Re / 2]))
         pr = lbm.lbm_default_params(T_over_Tc=wl_base.T_over_Tc, **WL.PAPER_EOS)
-        P = lambda r: _pressure(pr, r)
-        dP = P(r_in) - P(r_out)
-        res.append(dict(R0=R, rho_in=r_in, rho_out=r_out, R_e=Re, dP=dP, sigma=dP * Re,
+        dP = _pressure(pr, r_in) - _pressure(pr, r_out)
+        res.append(dict(R0=R, steps=steps, rho_in=r_in, rho_out=r_out, R_e=Re, dP=dP, sigma=dP * Re,
                         max_u=float(np.max(np.abs(u))), mass_drift=(m1 - m0) / m0))
     return res
 
@@ -138,11 +158,13 @@ def main():
     k = 10 if args.quick else 1
     lbm.load()
     static = WL.STATIC_DROP_2D
-    print(json.dumps({"workload": static.name, "laplace_fp64": laplace(static, (20, 30), static.steps // k)}), flush=True)
-    print(json.dumps(compare(static, static.steps // k)), flush=True)
-    print(json.dumps(compare(WL.DROP_IMPACT_2D, WL.DROP_IMPACT_2D.steps // k)), flush=True)
-    print(json.dumps(compare(WL.DROP_IMPACT_3D_SMALL, 1000 // k)), flush=True)
-
+    print(json.dumps({"workload": static.name, "laplace_fp64": laplace(static, (20, 25, 30), static.steps // k)}), flush=True)
+    print(json.dumps({"workload": static.name, "laplace_fp64": laplace(static, (20, 25, 30), 10 * static.steps // k)}), flush=True)
+    print(json.dumps(compare(static, [static.steps // k])), flush=True)
+    d2 = WL.DROP_IMPACT_2D
+    print(json.dumps(compare(d2, [c // k for c in (1000, 2500, 5000, 10000, 20000)])), flush=True)
+    d3 = WL.DROP_IMPACT_3D_SMALL
+    print(json.dumps(compare(d3, [c // k for c in (250, 500, 1000, 2000)])), flush=True)
 
 if __name__ == "__main__":
     main()

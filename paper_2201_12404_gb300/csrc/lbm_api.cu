@@ -9,37 +9,12 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_handle.h"
 #include "lbm_ops.h"
 
 using lbm::DevDomain;
 using lbm::Ops;
 using lbm::Phys;
-
-struct lbm_domain {
-  alignas(64) CUtensorMap aux_map;  // rho and s*psi halo tiles for the collide kernel's TMA load
-  lbm_params p{};
-  const Ops* ops = nullptr;
-  DevDomain dev{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int parity = 0;
-  int64_t steps = 0;
-  int64_t launches = 0;
-  bool poisoned = false;
-  std::string err;
-  // error flags: device word, pinned host mirror, event marking the mirror's copy
-  unsigned int* h_flags = nullptr;
-  cudaEvent_t flags_ev = nullptr;
-  bool flags_pending = false;
-  // timing
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  struct Mark { int kind; cudaEvent_t a, b; };
-  std::vector<Mark> marks;
-  double ms[2] = {0, 0};
-  int64_t cnt[2] = {0, 0};
-  bool record_gamma = false;
-};
 
 static thread_local std::string g_create_error = "no error";
 
@@ -192,9 +167,9 @@ lbm_status poll_flags(lbm_domain* h, bool wait) {
   return flags_status(h, *h->h_flags);
 }
 
-lbm_status enqueue_flag_copy(lbm_domain* h) {
-  LBM_CUDA(h, cudaMemcpyAsync(h->h_flags, h->dev.flags, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
-  LBM_CUDA(h, cudaEventRecord(h->flags_ev, h->stream));
+lbm_status enqueue_flag_copy(lbm_domain* h, cudaStream_t stream) {
+  LBM_CUDA(h, cudaMemcpyAsync(h->h_flags, h->dev.flags, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream));
+  LBM_CUDA(h, cudaEventRecord(h->flags_ev, stream));
   h->flags_pending = true;
   return LBM_OK;
 }
@@ -254,6 +229,11 @@ double bisect_p(const EosCoeffs& e, double target, double lo, double hi) {
 }
 
 }  // namespace
+
+lbm_status lbm_internal_enqueue_flag_copy(lbm_domain* h, cudaStream_t stream) {
+  if (h->flags_pending) return LBM_OK;
+  return enqueue_flag_copy(h, stream);
+}
 
 extern "C" {
 
@@ -472,7 +452,7 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
   }
   h->dev.gamma_out = saved.gamma_out;
   if (st != LBM_OK) return st;
-  if (nsteps > 0 && !h->flags_pending) return enqueue_flag_copy(h);
+  if (nsteps > 0 && !h->flags_pending) return enqueue_flag_copy(h, h->stream);
   return LBM_OK;
 }
 

@@ -113,39 +113,57 @@ __device__ __forceinline__ R entropic_gamma(R sA, R sB, R om) {
 }
 
 // Dynamic shared memory of the kernel: h_i of every node of the tile.
-template <int D, typename R>
+template <int D, typename R, int NT = Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz>
 constexpr size_t collide_dyn_smem() {
-  return (size_t)Lattice<D>::Q * Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz * sizeof(R);
+  return (size_t)Lattice<D>::Q * NT * sizeof(R);
 }
 
-template <int D, int P, typename S, typename R, typename A>
-__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
-collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) {
+// Halo-tile extents of a BX x BY x BZ tile.
+template <int D, int BX, int BY, int BZ> struct Halo {
+  static constexpr int HX = BX + 4, HY = BY + 4, HZ = D == 3 ? BZ + 4 : 1;
+  static constexpr int HN = HX * HY * HZ;
+};
+
+// One tile of pass 2 whose origin is (x0, y0, z0), run by the BX*BY*BZ threads of
+// the block.  kTma: the halo tile comes from a TMA copy of the tensor map `map`,
+// completed on `bar` (phase `phase`); otherwise each warp loads halo rows.
+// s_aux holds 2*HN values, s_h Q*BX*BY*BZ.
+template <int D, int BX, int BY, int BZ, int P, typename S, typename R, typename A, bool kTma>
+__device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorMap* map, int x0, int y0, int z0,
+                                             A* s_aux, R* s_h, unsigned long long* bar, uint32_t phase) {
   constexpr int Q = Lattice<D>::Q;
-  constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
   constexpr int NT = BX * BY * BZ;
-  constexpr int HX = BX + 4, HY = BY + 4, HZ = D == 3 ? BZ + 4 : 1;
+  constexpr int HX = Halo<D, BX, BY, BZ>::HX, HY = Halo<D, BX, BY, BZ>::HY, HZ = Halo<D, BX, BY, BZ>::HZ;
   constexpr int HN = HX * HY * HZ;
   constexpr R cs2 = (R)(1.0 / 3.0);
-  __shared__ __align__(128) A s_aux[2 * HN];  // [field][z][y][x]: rho, then s*psi
-  __shared__ __align__(8) unsigned long long tile_bar;
   const A* s_rho = s_aux;
   const A* s_psi = s_aux + HN;
-  // higher-order part h_i of every node of the tile, [i][thread] (dynamic: above 48 KB in float64)
-  extern __shared__ __align__(16) unsigned char smem_dyn[];
-  R* s_h = (R*)smem_dyn;
-
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = D == 3 ? blockIdx.z * BZ : 0;
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
   const Phys<R>& ph = phys<R>(d);
 
-  // ---- start the halo-tile copy: padded coordinates of the tile's halo origin are
-  //      the tile origin itself; x0 is a multiple of 32, so the box starts 16-byte aligned
-  if (tid == 0) mbar_init(&tile_bar, 1);
-  __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&tile_bar, (uint32_t)(2 * HN * sizeof(A)));
-    tma_load_tile<D>(s_aux, &aux_map, &tile_bar, x0, y0, z0);
+  // ---- stage rho and s*psi of the tile plus halo; padded coordinates of the halo
+  //      origin are the tile origin itself
+  if (kTma) {
+    // x0 is a multiple of BX (>= 32), so the box starts 16-byte aligned
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)(2 * HN * sizeof(A)));
+      tma_load_tile<D>(s_aux, map, bar, x0, y0, z0);
+    }
+  } else {
+    const A* a_rho = (const A*)d.aux;
+    const A* a_psi = a_rho + d.PN;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < HY * HZ; r += NT / 32) {
+      const int yp = y0 + r % HY, zp = z0 + r / HY;
+      const bool row_ok = yp < d.py && zp < d.pz;
+      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
+      for (int hx = lane; hx < HX; hx += 32) {
+        const bool ok = row_ok && x0 + hx < d.px;
+        s_aux[r * HX + hx] = ok ? a_rho[base + hx] : (A)1;
+        s_aux[HN + r * HX + hx] = ok ? a_psi[base + hx] : (A)0;
+      }
+    }
+    __syncthreads();
   }
 
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
@@ -155,11 +173,13 @@ collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) 
 
   R f[Q];
   if (active) gather<D, P, S, R>(d, x, y, z, f);
-  // every thread waits, so that the block cannot retire while the copy is in flight
-  if (!mbar_wait_bounded(&tile_bar, 0, kTileWaitPolls)) {
-    if (tid == 0) atomicOr(d.flags, 2u);
-    mbar_wait_bounded(&tile_bar, 0, kTileWaitPolls);
-    return;
+  if (kTma) {
+    // every thread waits, so that the block cannot retire while the copy is in flight
+    if (!mbar_wait_bounded(bar, phase, kTileWaitPolls)) {
+      if (tid == 0) atomicOr(d.flags, 2u);
+      mbar_wait_bounded(bar, phase, kTileWaitPolls);
+      return;
+    }
   }
   if (!active) return;
 
@@ -340,6 +360,21 @@ collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) 
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_pop<S, R>(Fo + dst_slot<D, P>(d, false, x, y, z, n, i), f[i]);
   }
+}
+
+template <int D, int P, typename S, typename R, typename A>
+__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
+collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) {
+  constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
+  __shared__ __align__(128) A s_aux[2 * Halo<D, BX, BY, BZ>::HN];  // [field][z][y][x]: rho, then s*psi
+  __shared__ __align__(8) unsigned long long tile_bar;
+  // higher-order part h_i of every node of the tile, [i][thread] (dynamic: above 48 KB in float64)
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  if (tid == 0) mbar_init(&tile_bar, 1);
+  __syncthreads();
+  collide_tile<D, BX, BY, BZ, P, S, R, A, true>(d, &aux_map, blockIdx.x * BX, blockIdx.y * BY,
+                                                 D == 3 ? blockIdx.z * BZ : 0, s_aux, (R*)smem_dyn, &tile_bar, 0);
 }
 
 }  // namespace lbm

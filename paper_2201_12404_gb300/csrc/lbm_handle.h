@@ -1,0 +1,41 @@
+// Host-side state behind an lbm_handle (shared by the host translation units).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_ops.h"
+
+struct lbm_domain {
+  alignas(64) CUtensorMap aux_map;  // rho and s*psi halo tiles for the collide kernel's TMA load
+  lbm_params p{};
+  const lbm::Ops* ops = nullptr;
+  lbm::DevDomain dev{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int parity = 0;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  bool poisoned = false;
+  std::string err;
+  // error flags: device word, pinned host mirror, event marking the mirror's copy
+  unsigned int* h_flags = nullptr;
+  cudaEvent_t flags_ev = nullptr;
+  bool flags_pending = false;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Mark { int kind; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  double ms[2] = {0, 0};
+  int64_t cnt[2] = {0, 0};
+  bool record_gamma = false;
+};
+
+// Mark the domain's error word as copied to the host after work enqueued on `stream`
+// (defined in lbm_api.cu); lbm_step / lbm_synchronize report it.
+lbm_status lbm_internal_enqueue_flag_copy(lbm_domain* h, cudaStream_t stream);

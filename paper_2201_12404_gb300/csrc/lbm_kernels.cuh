@@ -20,11 +20,8 @@ namespace lbm {
 // q is negated across a wall (no-slip image).
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, typename R, typename A>
-__global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d) {
+__device__ __forceinline__ void moments_eos_node(const DevDomain& d, int xp, int yp, int zp) {
   constexpr int Q = Lattice<D>::Q;
-  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
-  const int yp = blockIdx.y * blockDim.y + threadIdx.y;
-  const int zp = blockIdx.z * blockDim.z + threadIdx.z;
   if (xp >= d.nx + 4 || yp >= d.py || zp >= d.pz) return;
   bool flip = false;
   auto image = [&](int c, int n, int wlo, int whi) {
@@ -55,6 +52,12 @@ __global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d) {
     const R q = rho * ua * ua * ua;
     aux[(2 + a) * d.PN + pn] = (A)(flip ? -q : q);
   }
+}
+
+template <int D, int P, typename S, typename R, typename A>
+__global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d) {
+  moments_eos_node<D, P, S, R, A>(d, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+                                  blockIdx.z * blockDim.z + threadIdx.z);
 }
 
 }  // namespace lbm

@@ -93,6 +93,13 @@ def load():
                 "lbm_last_error": (ctypes.c_char_p, [H]),
                 "lbm_version": (ctypes.c_char_p, []),
                 "lbm_step_noalloc": (st, [P, ctypes.c_void_p, ctypes.c_int64]),
+                "lbm_batch_create": (st, [ctypes.POINTER(H), ctypes.c_int32, ctypes.POINTER(H)]),
+                "lbm_batch_step": (st, [H, ctypes.c_int64]),
+                "lbm_batch_synchronize": (st, [H]),
+                "lbm_batch_tune": (st, [H, ctypes.c_int32, ctypes.c_char_p]),
+                "lbm_batch_info": (st, [H] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+                "lbm_batch_destroy": (st, [H]),
+                "lbm_batch_last_error": (ctypes.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -260,3 +267,52 @@ class Domain:
 
     def lbm_last_error(self) -> str:
         return load().lbm_last_error(self.handle).decode()
+
+
+class Batch:
+    """Several D2Q9 domains advanced by one persistent launch (lbm_batch_*)."""
+
+    def __init__(self, domains):
+        L = load()
+        self.domains = list(domains)
+        arr = (ctypes.c_void_p * len(self.domains))(*[d.handle.value for d in self.domains])
+        h = ctypes.c_void_p()
+        st = L.lbm_batch_create(arr, len(self.domains), ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, L.lbm_batch_last_error(None).decode())
+        self.handle = h
+
+    def _c(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, load().lbm_batch_last_error(self.handle).decode())
+
+    def lbm_batch_step(self, nsteps: int):
+        self._c(load().lbm_batch_step(self.handle, int(nsteps)))
+
+    def lbm_batch_synchronize(self):
+        self._c(load().lbm_batch_synchronize(self.handle))
+
+    def lbm_batch_tune(self, trial_steps: int, cache_path=None):
+        self._c(load().lbm_batch_tune(self.handle, int(trial_steps), cache_path.encode() if cache_path else None))
+
+    def lbm_batch_info(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        self._c(load().lbm_batch_info(self.handle, *[ctypes.byref(x) for x in v]))
+        return dict(block=(v[0].value, v[1].value), grid=v[2].value, graph=bool(v[3].value))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
