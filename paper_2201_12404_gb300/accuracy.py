@@ -17,7 +17,11 @@ The static drop (Sec. 3.1.2) also reports the Laplace pressure jump
 Delta P = P(rho_in) - P(rho_out) times the equimolar radius for two radii, the
 two products being the same surface tension when Laplace's law holds.
 
-  python -m paper_2201_12404_gb300.accuracy [--quick]
+  python -m paper_2201_12404_gb300.accuracy [--quick] [--part coexistence]
+
+The coexistence sweep (Sec. 3.1.1) runs 16 flat-interface jobs of uneven sizes in one
+persistent batched launch and compares the bulk densities with the Maxwell
+construction.
 
 Prints one JSON object per workload.  Everything runs through the C ABI.
 """
@@ -144,6 +148,68 @@ def laplace(wl_base, radii, steps):
     return res
 
 
+def coexistence_sweep(n_jobs=16, cap_steps=50000, chunk=1000, tol=1e-5, seed=None):
+    """Flat-interface coexistence (Sec. 3.1.1) for n_jobs D2Q9 jobs of uneven sizes
+    (n_x = 64 (1 + k mod 4), n_y = 4 n_x, assigned to the temperatures by a seeded
+    shuffle), T/Tc evenly spaced over [0.5, 0.95], a liquid slab over the middle half of
+    n_y, nu = 0.1, float32, all advanced by one persistent batched launch per chunk
+    until max |rho(t + chunk) - rho(t)| / rho_l < tol for every job (or cap_steps).
+    The bulk densities (averages over the middle quarter of the slab and the quarter of
+    the domain farthest from it) are compared with the Maxwell construction."""
+    from . import inputs as I
+    seed = I.SEED_BASE if seed is None else seed
+    sizes = [64 * (1 + (k % 4)) for k in range(n_jobs)]
+    order = I.rng(seed).permutation(n_jobs)
+    trs = [0.5 + 0.45 * k / (n_jobs - 1) for k in range(n_jobs)]
+    doms, meta = [], []
+    try:
+        for k in range(n_jobs):
+            nx = sizes[order[k]]
+            ny = 4 * nx
+            Tr = trs[k]
+            rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=Tr, **WL.PAPER_EOS))
+            wl = WL.Workload(name=f"coex{k}", D=2, nx=nx, ny=ny, nz=1, T_over_Tc=Tr, kappa=0.005, nu_liquid=0.1,
+                             mu_ratio=0.0, R=1.0, U=0.0, film=0.0)
+            p = WL.params(wl, lbm.LBM_FP32, rv=rv, rl=rl)
+            d = lbm.Domain(p)
+            rho = I.slab((1, ny, nx), 1, ny / 4, 3 * ny / 4, rl, rv, 5.0)
+            d.lbm_init_fields(rho, np.zeros((2, 1, ny, nx)))
+            doms.append(d)
+            meta.append(dict(T_over_Tc=Tr, nx=nx, ny=ny, rho_l_maxwell=rl, rho_v_maxwell=rv))
+        prev = [d.lbm_read_macroscopic()[0] for d in doms]
+        steps, done = 0, [False] * n_jobs
+        t_gpu = 0.0
+        with lbm.Batch(doms) as b:
+            b.lbm_batch_tune(5)
+            info = b.lbm_batch_info()
+            while steps < cap_steps and not all(done):
+                t0 = time.perf_counter()
+                b.lbm_batch_step(chunk)
+                b.lbm_batch_synchronize()
+                t_gpu += time.perf_counter() - t0
+                steps += chunk
+                for k, d in enumerate(doms):
+                    r = d.lbm_read_macroscopic()[0]
+                    if not done[k] and np.max(np.abs(r - prev[k])) / meta[k]["rho_l_maxwell"] < tol:
+                        done[k] = True
+                        meta[k]["steady_at"] = steps
+                    prev[k] = r
+        nodes = sum(m["nx"] * m["ny"] for m in meta)
+        rows = []
+        for k, m in enumerate(meta):
+            r = prev[k][0]
+            ny = m["ny"]
+            liquid = float(np.mean(r[3 * ny // 8: 5 * ny // 8]))
+            vapour = float(np.mean(np.concatenate([r[: ny // 8], r[7 * ny // 8:]])))
+            rows.append(dict(m, rho_l=liquid, rho_v=vapour, err_l=liquid / m["rho_l_maxwell"] - 1,
+                             err_v=vapour / m["rho_v_maxwell"] - 1, steady=done[k]))
+        return dict(workload="D2Q9 flat-interface coexistence sweep, 16 jobs 64x256..256x1024, FP32, one batched launch",
+                    steps=steps, batch=info, batched_mlups=nodes * steps / t_gpu / 1e6, jobs=rows)
+    finally:
+        for d in doms:
+            d.close()
+
+
 def _pressure(p, rho):
     Tc = 0.0778 * p.a / (0.45724 * p.b * p.R)
     m = 0.37464 + 1.54226 * p.acentric - 0.26992 * p.acentric ** 2
@@ -154,9 +220,13 @@ def _pressure(p, rho):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="fewer steps (a smoke run)")
+    ap.add_argument("--part", default="all", help="all, laplace, precision or coexistence")
     args = ap.parse_args()
     k = 10 if args.quick else 1
     lbm.load()
+    if args.part == "coexistence":
+        print(json.dumps(coexistence_sweep(cap_steps=50000 // k)), flush=True)
+        return
     static = WL.STATIC_DROP_2D
     print(json.dumps({"workload": static.name, "laplace_fp64": laplace(static, (20, 25, 30), static.steps // k)}), flush=True)
     print(json.dumps({"workload": static.name, "laplace_fp64": laplace(static, (20, 25, 30), 10 * static.steps // k)}), flush=True)
@@ -165,6 +235,7 @@ def main():
     print(json.dumps(compare(d2, [c // k for c in (1000, 2500, 5000, 10000, 20000)])), flush=True)
     d3 = WL.DROP_IMPACT_3D_SMALL
     print(json.dumps(compare(d3, [c // k for c in (250, 500, 1000, 2000)])), flush=True)
+    print(json.dumps(coexistence_sweep(cap_steps=50000 // k)), flush=True)
 
 if __name__ == "__main__":
     main()
