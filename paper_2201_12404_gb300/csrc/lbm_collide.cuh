@@ -254,26 +254,26 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
 
   // ---- one-dimensional factors, index c+1: equilibrium X, extended equilibrium Xs,
   //      first-order dual d1 of the central Hermite basis
-  R X[3][3], Xs[3][3], d1[3][3];
+  // per-axis velocity, its square, and the extended-equilibrium variables xi*, zeta*
+  R uu[3], ua2[3], xs[3], zs[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (a < D) {
-      const R ua = u[a], u2 = ua * ua;
-      X[a][1] = (R)1 - cs2 - u2;
-      X[a][2] = (R)0.5 * (cs2 + u2 + ua);
-      X[a][0] = (R)0.5 * (cs2 + u2 - ua);
-      const R xi = ua + F[a] * inv_rho;
-      const R ze = cs2 + xi * xi + Phi[a] * inv_rho;
-      Xs[a][1] = (R)1 - ze;
-      Xs[a][2] = (R)0.5 * (ze + xi);
-      Xs[a][0] = (R)0.5 * (ze - xi);
-      d1[a][1] = (R)-2 * ua;
-      d1[a][2] = ua + (R)0.5;
-      d1[a][0] = ua - (R)0.5;
-    } else {
-      X[a][0] = X[a][2] = Xs[a][0] = Xs[a][2] = d1[a][0] = d1[a][1] = d1[a][2] = 0;
-      X[a][1] = Xs[a][1] = 1;
-    }
+    uu[a] = a < D ? u[a] : (R)0;
+    ua2[a] = uu[a] * uu[a];
+    xs[a] = a < D ? uu[a] + F[a] * inv_rho : (R)0;
+    zs[a] = a < D ? cs2 + xs[a] * xs[a] + Phi[a] * inv_rho : cs2;
+  }
+  // factor of index k = c+1 along one axis: equilibrium, extended equilibrium, first-order dual
+  auto eqf = [&](int k, int a) { return k == 1 ? (R)1 - cs2 - ua2[a] : (R)0.5 * (cs2 + ua2[a] + (k == 2 ? uu[a] : -uu[a])); };
+  auto stf = [&](int k, int a) { return k == 1 ? (R)1 - zs[a] : (R)0.5 * (zs[a] + (k == 2 ? xs[a] : -xs[a])); };
+  auto d1f = [&](int k, int a) { return k == 1 ? (R)-2 * uu[a] : uu[a] + (k == 2 ? (R)0.5 : (R)-0.5); };
+  // x-axis factors, used for every population
+  R X[3], Xs[3], d1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    X[k] = eqf(k, 0);
+    Xs[k] = stf(k, 0);
+    d1[k] = d1f(k, 0);
   }
   // second-order central Hermite moments; the shear part keeps the off-diagonals
   // and the deviatoric diagonal a_aa - trace/D
@@ -290,42 +290,61 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
   // s = d0_x C0 + d1_x C1 + d2_x C2 with d2 = {-1 at c = 0, 1/2 at c = +-1}.
   struct Row { R ryz, rsyz, C0, C1, C2; };
   auto row_coef = [&](int iy, int iz) {
-    const R Z0 = D == 3 ? X[2][iz] : (R)1, Zs = D == 3 ? Xs[2][iz] : (R)1;
-    const R Z1 = D == 3 ? d1[2][iz] : (R)0;
+    const R Z0 = D == 3 ? eqf(iz, 2) : (R)1, Zs = D == 3 ? stf(iz, 2) : (R)1;
+    const R Z1 = D == 3 ? d1f(iz, 2) : (R)0;
     const R Z2 = D == 3 ? (iz == 1 ? (R)-1 : (R)0.5) : (R)0;
-    const R Y0 = X[1][iy], Y1 = d1[1][iy], Y2 = iy == 1 ? (R)-1 : (R)0.5;
+    const R Y0 = eqf(iy, 1), Y1 = d1f(iy, 1), Y2 = iy == 1 ? (R)-1 : (R)0.5;
     Row r;
     r.ryz = rho * Y0 * Z0;
-    r.rsyz = rho * Xs[1][iy] * Zs;
+    r.rsyz = rho * stf(iy, 1) * Zs;
     r.C0 = ayz * Y1 * Z1 + devy * Y2 * Z0 + (D == 3 ? devz * Y0 * Z2 : (R)0);
     r.C1 = axy * Y1 * Z0 + (D == 3 ? axz * Y0 * Z1 : (R)0);
     r.C2 = devx * Y0 * Z0;
     return r;
   };
 
-  // ---- pass A: entropic sums, h to shared memory, g = f - omega s + f* - f^eq in place of f
-  R sA = 0, sB = 0, fmin = (R)1;
+  // ---- pass A: entropic sums, h to shared memory, g = f - omega s + f* - f^eq
+  //      = h + (1 - omega) s + f* in place of f.  Every f*_i is positive exactly when
+  //      rho and the nine one-dimensional factors Xs are (each axis's three factors
+  //      sum to one, so they cannot all be negative).  The weight 1/f*_i factors as
+  //      1/(rho Ys Zs) times 1/Xs, so a row's three terms are summed with the x
+  //      reciprocals and scaled once by the row's; partial sums per iy keep the
+  //      dependency chains short.
+  R fmin = rho;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fmin = fmin < stf(k, a) ? fmin : stf(k, a);
+  const R one_m_om = (R)1 - om;
+  R sAy[3] = {0, 0, 0}, sBy[3] = {0, 0, 0};
+  R iXs[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) iXs[k] = rcp_fast<R>(Xs[k]);
 #pragma unroll
   for (int iz = 0; iz < (D == 3 ? 3 : 1); ++iz) {
 #pragma unroll
     for (int iy = 0; iy < 3; ++iy) {
       const Row r = row_coef(iy, iz);
+      R tA = 0, tB = 0;
 #pragma unroll
       for (int ix = 0; ix < 3; ++ix) {
         const int i = ix + 3 * iy + 9 * iz;
-        const R feq = r.ryz * X[0][ix];
-        const R fst = r.rsyz * Xs[0][ix];
-        const R s = X[0][ix] * r.C0 + d1[0][ix] * r.C1 + (ix == 1 ? -r.C2 : (R)0.5 * r.C2);
+        const R feq = r.ryz * X[ix];
+        const R fst = r.rsyz * Xs[ix];
+        const R s = X[ix] * r.C0 + d1[ix] * r.C1 + (ix == 1 ? -r.C2 : (R)0.5 * r.C2);
         const R hh = f[i] - feq - s;
-        fmin = fmin < fst ? fmin : fst;
-        const R hr = hh * rcp_fast<R>(fst);
-        sA += s * hr;
-        sB += hh * hr;
+        const R hr = hh * iXs[ix];
+        tA += s * hr;
+        tB += hh * hr;
         s_h[i * NT + tid] = hh;
-        f[i] = f[i] - om * s + (fst - feq);
+        f[i] = hh + one_m_om * s + fst;
       }
+      const R irs = rcp_fast<R>(r.rsyz);
+      sAy[iy] += irs * tA;
+      sBy[iy] += irs * tB;
     }
   }
+  const R sA = (sAy[0] + sAy[1]) + sAy[2], sB = (sBy[0] + sBy[1]) + sBy[2];
 
   R gamma;
   if (d.gamma_mode == 1) {
