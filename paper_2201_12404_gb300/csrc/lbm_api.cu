@@ -11,6 +11,7 @@
 #include "../../include/lbm.h"
 #include "lbm_handle.h"
 #include "lbm_ops.h"
+#include "lbm_phys.h"
 
 using lbm::DevDomain;
 using lbm::Ops;
@@ -24,23 +25,9 @@ const char* kVersion = "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP3
 
 bool is_wall(int v) { return v == LBM_BC_BOUNCEBACK; }
 
-struct EosCoeffs { double RT, b, aalpha, Tc; };
-
-EosCoeffs eos_coeffs(const lbm_params& p) {
-  EosCoeffs e;
-  e.Tc = 0.0778 * p.a / (0.45724 * p.b * p.R);
-  const double T = p.T_over_Tc * e.Tc;
-  const double m = 0.37464 + 1.54226 * p.acentric - 0.26992 * p.acentric * p.acentric;
-  const double s = 1.0 + m * (1.0 - std::sqrt(p.T_over_Tc));
-  e.RT = p.R * T;
-  e.b = p.b;
-  e.aalpha = p.a * s * s;
-  return e;
-}
-
-double pr_p(const EosCoeffs& e, double rho) {
-  return rho * e.RT / (1.0 - e.b * rho) - e.aalpha * rho * rho / (1.0 + 2.0 * e.b * rho - e.b * e.b * rho * rho);
-}
+using lbm::EosCoeffs;
+using lbm::eos_coeffs;
+using lbm::pr_p;
 
 std::string validate(const lbm_params* p) {
   if (!p) return "params is NULL";
@@ -182,7 +169,7 @@ lbm_status launch_k(lbm_domain* h, int kind) {
     LBM_CUDA(h, cudaEventRecord(a, h->stream));
   }
   if (kind == 0) h->ops->moments_eos(h->dev, h->parity, h->stream);
-  else h->ops->collide_stream(h->dev, h->aux_map, h->parity, h->stream);
+  else h->ops->collide_stream(h->dev, h->maps, h->parity, h->stream);
   h->launches += 1;
   LBM_CUDA(h, cudaGetLastError());
   if (h->timing) {
@@ -322,30 +309,8 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
     d.wall_lo[a] = active && is_wall(p->bc[2 * a]);
     d.wall_hi[a] = active && is_wall(p->bc[2 * a + 1]);
   }
-  Phys<double>& pd = d.pd;
-  pd.kappa = p->kappa;
-  for (int a = 0; a < 3; ++a) pd.g[a] = a < s.D ? p->body_force[a] : 0.0;
-  pd.nu_v = p->nu_vapour;
-  pd.dnu = p->nu_liquid - p->nu_vapour;
-  pd.rho_v = p->rho_vapour;
-  pd.inv_drho = 1.0 / (p->rho_liquid - p->rho_vapour);
-  const EosCoeffs e = eos_coeffs(*p);
-  pd.RT = e.RT; pd.b = e.b; pd.aalpha = e.aalpha;
-  pd.gamma_value = p->gamma_value;
-  // interface band: densities between the phases, 1% of the density jump inside each bulk value
-  const double span = p->rho_liquid - p->rho_vapour;
-  pd.band_lo = p->rho_vapour + 0.01 * span;
-  pd.band_hi = p->rho_liquid - 0.01 * span;
-  Phys<float>& pf = d.pf;
-  pf.kappa = (float)pd.kappa;
-  for (int a = 0; a < 3; ++a) pf.g[a] = (float)pd.g[a];
-  pf.nu_v = (float)pd.nu_v; pf.dnu = (float)pd.dnu; pf.rho_v = (float)pd.rho_v; pf.inv_drho = (float)pd.inv_drho;
-  pf.RT = (float)pd.RT; pf.b = (float)pd.b; pf.aalpha = (float)pd.aalpha;
-  pf.gamma_value = (float)pd.gamma_value;
-  pf.band_lo = (float)pd.band_lo; pf.band_hi = (float)pd.band_hi;
-  d.gamma_mode = p->gamma_mode;
-  d.eos_fp64 = p->eos_fp64;
-  lbm::fill_slot_offsets(d, s.D);
+  lbm::fill_phys(d, *p, s.D);
+  lbm::fill_slot_offsets(d, s.D, h->ops->pop_bytes);
 
   auto bail = [&](cudaError_t err, const char* where) {
     g_create_error = std::string(where) + ": " + cudaGetErrorString(err);
@@ -375,7 +340,7 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
   if ((err = cudaMemsetAsync(d.aux, 0, s.aux_bytes, h->stream)) != cudaSuccess) return bail(err, "cudaMemset(aux)");
   {
     const char* why = nullptr;
-    if (!lbm::make_aux_map(&h->aux_map, d, s.D, h->ops->aux_bytes, &why)) {
+    if (!lbm::make_tile_maps(&h->maps, d, s.D, h->ops->aux_bytes, &why)) {
       g_create_error = why;
       lbm_destroy(h);
       return LBM_ERR_CUDA;

@@ -48,7 +48,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* er
 
 template <int BX, int BY, typename S, typename R, typename A>
 __global__ void __launch_bounds__(BX * BY) batch_persistent_kernel(BatchArgs a) {
-  __shared__ __align__(128) A s_aux[2 * Halo<2, BX, BY, 1>::HN];
+  __shared__ __align__(128) Two<A> s_aux[Halo<2, BX, BY, 1>::HN];
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   R* s_h = (R*)smem_dyn;
   for (int s = 0; s < a.nsteps; ++s) {
@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(BX * BY) batch_persistent_kernel(BatchArgs a) 
       const BatchItem w = a.k2[it];
       const DevDomain& d = a.jobs[w.job];
       if (((a.parity[w.job] + s) & 1) == 0)
-        collide_tile<2, BX, BY, 1, 0, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, s_h, nullptr, 0);
+        collide_tile<2, BX, BY, 1, 0, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, s_h, nullptr, 0);
       else
-        collide_tile<2, BX, BY, 1, 1, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, s_h, nullptr, 0);
+        collide_tile<2, BX, BY, 1, 1, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, s_h, nullptr, 0);
     }
     if (!grid_barrier(a.barrier, a.error)) return;
   }

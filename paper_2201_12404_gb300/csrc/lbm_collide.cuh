@@ -60,21 +60,62 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint3
   return false;
 }
 
-// Tile copy of a D-dimensional halo box of the two staged fields (rank D + 1).
-template <int D>
+// Tile copy of a D-dimensional halo box of (rho, psi) pairs: float32 pairs are
+// 8-byte elements of a rank-D map, float64 pairs the innermost dimension (2) of a
+// rank-(D + 1) map.
+template <int D, typename A>
 __device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z) {
-  if (D == 3) {
+  if (sizeof(A) == 4 && D == 3) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+  } else if (sizeof(A) == 4) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+  } else if (D == 3) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(0), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
   } else {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(0), "r"(smem_u32(bar))
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(0), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
   }
 }
+
+// Tile copy of the q_a box of axis a (rank-(D + 1) map over the q planes).
+template <int D>
+__device__ __forceinline__ void tma_load_q(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z, int a) {
+  if (D == 3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(a), "r"(smem_u32(bar))
+        : "memory");
+  } else {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(a), "r"(smem_u32(bar))
+        : "memory");
+  }
+}
+
+// Asynchronous 4- or 8-byte copy global -> shared (cp.async; a population is
+// one 4- or 8-byte word), completion tracked per thread by commit/wait groups.
+template <int kBytes>
+__device__ __forceinline__ void cp_async_word(void* smem, const void* gmem) {
+  static_assert(kBytes == 4 || kBytes == 8, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(smem)), "l"(gmem), "n"(kBytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Orders this thread's earlier shared-memory accesses (made visible to it by a
+// barrier) before its later TMA writes to the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Polls of the tile barrier before a block reports a timeout (bit 1 of the
 // error word) and stops; far above any real copy latency.
@@ -112,6 +153,13 @@ __device__ __forceinline__ R entropic_gamma(R sA, R sB, R om) {
   return (R)(tw - (2.0 - tw) * ratio);
 }
 
+// Dynamic shared memory of the persistent kernel: h_i and the staged
+// populations of every node of the tile.
+template <int D, typename S, typename R, int NT = Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz>
+constexpr size_t persistent_dyn_smem() {
+  return (size_t)Lattice<D>::Q * NT * (sizeof(R) + sizeof(S));
+}
+
 // Dynamic shared memory of the kernel: h_i of every node of the tile.
 template <int D, typename R, int NT = Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz>
 constexpr size_t collide_dyn_smem() {
@@ -122,36 +170,83 @@ constexpr size_t collide_dyn_smem() {
 template <int D, int BX, int BY, int BZ> struct Halo {
   static constexpr int HX = BX + 4, HY = BY + 4, HZ = D == 3 ? BZ + 4 : 1;
   static constexpr int HN = HX * HY * HZ;
+  // q_a box: the tile with one node around it in y and z, two in x (alignment)
+  static constexpr int QX = BX + 4, QY = BY + 2, QZ = D == 3 ? BZ + 2 : 1;
+  static constexpr int QB = QX * QY * QZ;
+  // elements of type T between consecutive q boxes in shared memory (128-byte steps)
+  template <typename T> static __host__ __device__ constexpr int qstride() { return (int)((QB * sizeof(T) + 127) / 128 * 128 / sizeof(T)); }
+};
+
+// Issue the TMA copies of one tile's staged fields, all completing on `bar`: the
+// (rho, psi) halo tile into s_aux and the D q_a boxes into s_q.  Called by one thread.
+template <int D, int BX, int BY, int BZ, typename A>
+__device__ __forceinline__ void tma_load_fields(const TileMaps* maps, Two<A>* s_aux, A* s_q, unsigned long long* bar,
+                                                int x0, int y0, int z0) {
+  using H = Halo<D, BX, BY, BZ>;
+  mbar_arrive_expect_tx(bar, (uint32_t)(H::HN * sizeof(Two<A>) + D * H::QB * sizeof(A)));
+  tma_load_tile<D, A>(s_aux, &maps->aux, bar, x0, y0, z0);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    tma_load_q<D>(s_q + a * H::template qstride<A>(), &maps->q, bar, x0, y0 + 1, D == 3 ? z0 + 1 : 0, a);
+}
+
+// Rows of populations sharing (cy, cz), paired for two-lane arithmetic.  Pair
+// k < kYPairs holds the rows cy = -1 (lane x) and cy = +1 (lane y) at cz = k - 1
+// (2-D: cz = 0); in 3-D pair 3 holds the rows cz = -1 and cz = +1 at cy = 0.  The
+// row cy = cz = 0 stays single.  Both lanes of a pair have the same weight w_i.
+template <int D> struct RowPairs {
+  static constexpr int kYPairs = D == 3 ? 3 : 1;
+  static constexpr int kPairs = D == 3 ? 4 : 1;
+  // population index of lane `lane` (0: x, 1: y) of pair k at x index ix = cx + 1
+  static __host__ __device__ constexpr int pop(int k, int lane, int ix) {
+    return D == 2 ? ix + 6 * lane : (k < 3 ? ix + 6 * lane + 9 * k : ix + 3 + 18 * lane);
+  }
+  static __host__ __device__ constexpr int single(int ix) { return D == 3 ? ix + 12 : ix + 3; }
+};
+
+struct NoHooks {
+  __device__ void prefetch() const {}
+  __device__ void aux() const {}
 };
 
 // One tile of pass 2 whose origin is (x0, y0, z0), run by the BX*BY*BZ threads of
-// the block.  kTma: the halo tile comes from a TMA copy of the tensor map `map`,
-// completed on `bar` (phase `phase`); otherwise each warp loads halo rows.
-// s_aux holds 2*HN values, s_h Q*BX*BY*BZ.
-template <int D, int BX, int BY, int BZ, int P, typename S, typename R, typename A, bool kTma>
-__device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorMap* map, int x0, int y0, int z0,
-                                             A* s_aux, R* s_h, unsigned long long* bar, uint32_t phase) {
+// the block.  kTma: the halo tile and the q boxes (s_q) come from TMA copies of
+// the tensor maps `maps`, completed on `bar` (phase `phase`); otherwise each warp
+// loads halo rows and q comes from global memory.
+// kStaged (with kTma): the caller has already issued this tile's halo copy and
+// staged its populations in s_f ([i][thread], cp.async completed); once every
+// thread has read its populations the tile calls hooks.prefetch() (the next
+// tile's populations into s_f), and once the block is done with the halo tile it
+// calls hooks.aux() (the next halo copy into s_aux) after a block barrier that
+// every thread of the block reaches.
+// s_aux holds the HN (rho, psi) pairs of the halo tile; s_h Q*BX*BY*BZ values of h:
+// the pair rows first (Two<R> [pair*3 + ix][thread]), then the single row.
+// Returns false when the halo copy did not arrive within the poll limit.
+template <int D, int BX, int BY, int BZ, int P, typename S, typename R, typename A, bool kTma,
+          bool kStaged = false, typename Hooks = NoHooks>
+__device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps* maps, int x0, int y0, int z0,
+                                             Two<A>* s_aux, A* s_q, R* s_h, unsigned long long* bar, uint32_t phase,
+                                             const S* s_f = nullptr, const Hooks& hooks = Hooks()) {
   constexpr int Q = Lattice<D>::Q;
   constexpr int NT = BX * BY * BZ;
   constexpr int HX = Halo<D, BX, BY, BZ>::HX, HY = Halo<D, BX, BY, BZ>::HY, HZ = Halo<D, BX, BY, BZ>::HZ;
   constexpr int HN = HX * HY * HZ;
+  constexpr int NY = RowPairs<D>::kYPairs, NP = RowPairs<D>::kPairs;
+  using RP = RowPairs<D>;
+  using R2 = Two<R>;
   constexpr R cs2 = (R)(1.0 / 3.0);
-  const A* s_rho = s_aux;
-  const A* s_psi = s_aux + HN;
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
   const Phys<R>& ph = phys<R>(d);
+  R2* s_h2 = (R2*)s_h;                  // [NP * 3][NT]
+  R* s_h1 = s_h + 2 * (NP * 3) * NT;    // [3][NT]
 
-  // ---- stage rho and s*psi of the tile plus halo; padded coordinates of the halo
+  // ---- stage (rho, psi) of the tile plus halo; padded coordinates of the halo
   //      origin are the tile origin itself
-  if (kTma) {
+  if (kTma && !kStaged) {
     // x0 is a multiple of BX (>= 32), so the box starts 16-byte aligned
-    if (tid == 0) {
-      mbar_arrive_expect_tx(bar, (uint32_t)(2 * HN * sizeof(A)));
-      tma_load_tile<D>(s_aux, map, bar, x0, y0, z0);
-    }
-  } else {
-    const A* a_rho = (const A*)d.aux;
-    const A* a_psi = a_rho + d.PN;
+    if (tid == 0) tma_load_fields<D, BX, BY, BZ, A>(maps, s_aux, s_q, bar, x0, y0, z0);
+  } else if (!kTma) {
+    const Two<A>* a2 = (const Two<A>*)d.aux;
     const int lane = tid & 31, warp = tid >> 5;
     for (int r = warp; r < HY * HZ; r += NT / 32) {
       const int yp = y0 + r % HY, zp = z0 + r / HY;
@@ -159,8 +254,7 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
       const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
       for (int hx = lane; hx < HX; hx += 32) {
         const bool ok = row_ok && x0 + hx < d.px;
-        s_aux[r * HX + hx] = ok ? a_rho[base + hx] : (A)1;
-        s_aux[HN + r * HX + hx] = ok ? a_psi[base + hx] : (A)0;
+        s_aux[r * HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
       }
     }
     __syncthreads();
@@ -169,78 +263,121 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
   const bool active = x < d.nx && y < d.ny && z < d.nz;
   const long long n = node_of(d, x, y, z);
-  const bool inner = interior<D>(d, x, y, z);
+  const bool fast = P == 0 || fast_links<D>(d, x, y, z);
 
   R f[Q];
-  if (active) gather<D, P, S, R>(d, x, y, z, f);
+  if (kStaged) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = active ? ld_pop<S, R>(s_f + i * NT + tid) : (R)wq<D>(i);
+  } else if (active) {
+    gather<D, P, S, R>(d, x, y, z, f);
+  }
+  bool tile_ok = true;
   if (kTma) {
     // every thread waits, so that the block cannot retire while the copy is in flight
-    if (!mbar_wait_bounded(bar, phase, kTileWaitPolls)) {
+    tile_ok = mbar_wait_bounded(bar, phase, kTileWaitPolls);
+    if (!kStaged && !tile_ok) {
       if (tid == 0) atomicOr(d.flags, 2u);
       mbar_wait_bounded(bar, phase, kTileWaitPolls);
-      return;
+      return false;
     }
   }
-  if (!active) return;
+  if (!kStaged && !active) return true;
+
+  R2 fp[NP][3];
+  R fs[3];
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) fp[k][ix] = two<R>(f[RP::pop(k, 0, ix)], f[RP::pop(k, 1, ix)]);
+    fs[ix] = f[RP::single(ix)];
+  }
 
   // ---- rho, j, Pi from row sums: r0 = f- + f0 + f+, r1 = f+ - f-, r2 = f+ + f-
-  R rho = 0, jx = 0, jy = 0, jz = 0, Pxx = 0, Pyy = 0, Pzz = 0, Pxy = 0, Pxz = 0, Pyz = 0;
+  const R2 zero2 = both<R>((R)0), sgn = two<R>((R)-1, (R)1);
+  R2 RHO = zero2, JX = zero2, PXX = zero2, JY = zero2, PXY = zero2, PYY = zero2;
+  R2 JZ = zero2, PXZ = zero2, PZZ = zero2, PYZ = zero2;
 #pragma unroll
-  for (int row = 0; row < Q / 3; ++row) {
-    const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
-    const R fm = f[3 * row], f0 = f[3 * row + 1], fp = f[3 * row + 2];
-    const R r2 = fm + fp, r0 = r2 + f0, r1 = fp - fm;
-    rho += r0; jx += r1; Pxx += r2;
-    if (cy != 0) { jy += cy > 0 ? r0 : -r0; Pxy += cy > 0 ? r1 : -r1; Pyy += r0; }
-    if (cz != 0) { jz += cz > 0 ? r0 : -r0; Pxz += cz > 0 ? r1 : -r1; Pzz += r0; }
-    if (cy * cz != 0) Pyz += cy * cz > 0 ? r0 : -r0;
+  for (int k = 0; k < NP; ++k) {
+    const R2 r2 = add2(fp[k][0], fp[k][2]), r0 = add2(r2, fp[k][1]), r1 = sub2(fp[k][2], fp[k][0]);
+    RHO = add2(RHO, r0); JX = add2(JX, r1); PXX = add2(PXX, r2);
+    if (k < NY) {  // lanes cy = -1, +1 at cz = k - 1
+      JY = fma2(sgn, r0, JY); PXY = fma2(sgn, r1, PXY); PYY = add2(PYY, r0);
+      if (D == 3 && k != 1) {
+        if (k == 0) { JZ = sub2(JZ, r0); PXZ = sub2(PXZ, r1); PYZ = fma2(two<R>((R)1, (R)-1), r0, PYZ); }
+        else { JZ = add2(JZ, r0); PXZ = add2(PXZ, r1); PYZ = fma2(sgn, r0, PYZ); }
+        PZZ = add2(PZZ, r0);
+      }
+    } else {       // lanes cz = -1, +1 at cy = 0
+      JZ = fma2(sgn, r0, JZ); PXZ = fma2(sgn, r1, PXZ); PZZ = add2(PZZ, r0);
+    }
   }
+  const R s2 = fs[0] + fs[2], s0 = s2 + fs[1], s1 = fs[2] - fs[0];
+  const R rho = (RHO.x + RHO.y) + s0;
+  const R jx = (JX.x + JX.y) + s1, Pxx = (PXX.x + PXX.y) + s2;
+  const R jy = JY.x + JY.y, Pxy = PXY.x + PXY.y, Pyy = PYY.x + PYY.y;
+  const R jz = D == 3 ? JZ.x + JZ.y : (R)0, Pxz = D == 3 ? PXZ.x + PXZ.y : (R)0;
+  const R Pzz = D == 3 ? PZZ.x + PZZ.y : (R)0, Pyz = D == 3 ? PYZ.x + PYZ.y : (R)0;
   const R inv_rho = (R)1 / rho;
   const R u[3] = {jx * inv_rho, jy * inv_rho, jz * inv_rho};
+  // every staged population has been consumed: s_f may take the next tile's
+  if (kStaged) hooks.prefetch();
 
   // ---- force: dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g, sums over the
-  //      lattice links row by row with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz)
+  //      lattice links row by row with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz).  The
+  //      two lanes carry G3[rho] (x) and G4[psi] (y): a link term 2 rho(r+c) - rho(r+2c)
+  //      and (4/3) psi(r+c) - (1/6) psi(r+2c) is (2, 4/3) times v(r+c) + (-1/2, -1/8) v(r+2c),
+  //      the common (2, 4/3) applied once at the end.
   const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
-  R g4x = 0, g4y = 0, g4z = 0, g3x = 0, g3y = 0, g3z = 0;
+  const R2 cb = two<R>((R)-0.5, (R)-0.125);
+  R2 GX = zero2, GY = zero2, GZ = zero2;
 #pragma unroll
   for (int row = 0; row < Q / 3; ++row) {
     const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
     const R wyz = (cy == 0 ? (R)2 : (R)0.5) * (D == 3 ? (cz == 0 ? (R)(2.0 / 3.0) : (R)(1.0 / 6.0)) : (R)1);
     const int orow = HX * (cy + HY * cz);
-    const A* pp = s_psi + sc + orow;
-    const A* pr = s_rho + sc + orow;
-    const A* pp2 = s_psi + sc + 2 * orow;
-    const A* pr2 = s_rho + sc + 2 * orow;
-    // t4 and t3 summed over the row with the x weights 1/6, 2/3, 1/6 and signs -1, 0, +1
-    R rowm4, row04, rowp4, rowm3, row03, rowp3;
-    {
-      const R pm = fabs((R)pp[-1]), p0 = fabs((R)pp[0]), pq = fabs((R)pp[1]);
-      const R pm2 = fabs((R)pp2[-2]), p02 = fabs((R)pp2[0]), pq2 = fabs((R)pp2[2]);
-      rowm4 = (R)(4.0 / 3.0) * pm - (R)(1.0 / 6.0) * pm2;
-      row04 = (row == (Q / 3) / 2) ? (R)0 : (R)(4.0 / 3.0) * p0 - (R)(1.0 / 6.0) * p02;
-      rowp4 = (R)(4.0 / 3.0) * pq - (R)(1.0 / 6.0) * pq2;
-      rowm3 = (R)2 * (R)pr[-1] - (R)pr2[-2];
-      row03 = (row == (Q / 3) / 2) ? (R)0 : (R)2 * (R)pr[0] - (R)pr2[0];
-      rowp3 = (R)2 * (R)pr[1] - (R)pr2[2];
+    const Two<A>* p1 = s_aux + sc + orow;
+    const Two<A>* p2 = s_aux + sc + 2 * orow;
+    auto v = [](const Two<A>& a) { return two<R>((R)a.x, (R)a.y); };
+    // row terms at cx = -1 and +1 (x weights 1/6, signs -1, +1) and cx = 0 (weight 2/3)
+    const R2 tm = fma2(cb, v(p2[-2]), v(p1[-1]));
+    const R2 tp = fma2(cb, v(p2[2]), v(p1[1]));
+    GX = fma2(both<R>(wyz * (R)(1.0 / 6.0)), sub2(tp, tm), GX);
+    R2 srow;
+    if (row == (Q / 3) / 2) {
+      srow = mul2(both<R>(wyz * (R)(1.0 / 6.0)), add2(tp, tm));
+    } else {
+      const R2 t0 = fma2(cb, v(p2[0]), v(p1[0]));
+      srow = fma2(both<R>(wyz * (R)(1.0 / 6.0)), add2(tp, tm), mul2(both<R>(wyz * (R)(2.0 / 3.0)), t0));
     }
-    // x-component: (+1) - (-1) with weight 1/6; y, z: weighted row sum 1/6, 2/3, 1/6
-    g4x += wyz * (R)(1.0 / 6.0) * (rowp4 - rowm4);
-    g3x += wyz * (R)(1.0 / 6.0) * (rowp3 - rowm3);
-    const R s4 = wyz * ((R)(1.0 / 6.0) * (rowp4 + rowm4) + (R)(2.0 / 3.0) * row04);
-    const R s3 = wyz * ((R)(1.0 / 6.0) * (rowp3 + rowm3) + (R)(2.0 / 3.0) * row03);
-    if (cy != 0) { g4y += cy > 0 ? s4 : -s4; g3y += cy > 0 ? s3 : -s3; }
-    if (D == 3 && cz != 0) { g4z += cz > 0 ? s4 : -s4; g3z += cz > 0 ? s3 : -s3; }
+    if (cy != 0) GY = cy > 0 ? add2(GY, srow) : sub2(GY, srow);
+    if (D == 3 && cz != 0) GZ = cz > 0 ? add2(GZ, srow) : sub2(GZ, srow);
   }
-  const R spsi_c = (R)s_psi[sc];
+  // s psi at the node: psi from the tile, s from the node's density in the tile
+  const Two<A> c_aux = s_aux[sc];
+  const R spsi_c = psi_sign<R>(ph, (R)c_aux.x) * (R)c_aux.y;
+  const R2 wf = two<R>((R)2 * ph.kappa * rho, (R)(8.0 / 3.0) * spsi_c);  // (kappa rho, 2 s psi) * (2, 4/3)
   R F[3];
-  F[0] = -((R)2 * spsi_c * g4x + ph.kappa * rho * g3x) + rho * ph.g[0];
-  F[1] = -((R)2 * spsi_c * g4y + ph.kappa * rho * g3y) + rho * ph.g[1];
-  F[2] = D == 3 ? -((R)2 * spsi_c * g4z + ph.kappa * rho * g3z) + rho * ph.g[2] : (R)0;
+  {
+    const R2 tx = mul2(wf, GX), ty = mul2(wf, GY), tz = mul2(wf, GZ);
+    F[0] = rho * ph.g[0] - (tx.x + tx.y);
+    F[1] = rho * ph.g[1] - (ty.x + ty.y);
+    F[2] = D == 3 ? rho * ph.g[2] - (tz.x + tz.y) : (R)0;
+  }
 
   // ---- Phi_aa = (1 - omega/2) d_a q_a, central difference
   const R om = omega_of<R>(ph, rho);
   R Phi[3] = {0, 0, 0};
-  {
+  if (kTma) {
+    using H = Halo<D, BX, BY, BZ>;
+    const int qc = (threadIdx.x + 2) + H::QX * ((threadIdx.y + 1) + H::QY * (D == 3 ? threadIdx.z + 1 : 0));
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const A* qa = s_q + a * H::template qstride<A>() + qc;
+      const int e = a == 0 ? 1 : (a == 1 ? H::QX : H::QX * H::QY);
+      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[e] - (R)qa[-e]) * (R)0.5;
+    }
+  } else {
     const A* a_q = (const A*)d.aux + 2 * d.PN;
     const long long pc = pnode_of<D>(d, x, y, z);
     const long long sy = d.px, sz = (long long)d.px * d.py;
@@ -251,30 +388,37 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
       Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc + e] - (R)qa[pc - e]) * (R)0.5;
     }
   }
+  if (kStaged) {
+    // the block is done with the staged fields (a block-wide vote on the copy's arrival)
+    if (__syncthreads_or(!tile_ok)) {
+      if (tid == 0) atomicOr(d.flags, 2u);
+      mbar_wait_bounded(bar, phase, kTileWaitPolls);
+      return false;
+    }
+    hooks.aux();
+    if (!active) return true;
+  }
 
-  // ---- one-dimensional factors, index c+1: equilibrium X, extended equilibrium Xs,
-  //      first-order dual d1 of the central Hermite basis
-  // per-axis velocity, its square, and the extended-equilibrium variables xi*, zeta*
-  R uu[3], ua2[3], xs[3], zs[3];
+  // ---- one-dimensional factors per axis, index k = c+1: equilibrium E, extended
+  //      equilibrium St, first-order dual d1 of the central Hermite basis (the
+  //      second-order dual is d2 = {1/2, -1, 1/2})
+  //      Each axis keeps u_a, he = (cs^2 + u_a^2)/2, xi*_a and hs = zeta*_a/2; the
+  //      factors are formed where they are used (fewer live registers).
+  R ua[3], he[3], xs[3], hs[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    uu[a] = a < D ? u[a] : (R)0;
-    ua2[a] = uu[a] * uu[a];
-    xs[a] = a < D ? uu[a] + F[a] * inv_rho : (R)0;
-    zs[a] = a < D ? cs2 + xs[a] * xs[a] + Phi[a] * inv_rho : cs2;
+    ua[a] = a < D ? u[a] : (R)0;
+    he[a] = (R)0.5 * (cs2 + ua[a] * ua[a]);
+    xs[a] = a < D ? ua[a] + F[a] * inv_rho : (R)0;
+    hs[a] = (R)0.5 * (a < D ? cs2 + xs[a] * xs[a] + Phi[a] * inv_rho : cs2);
   }
-  // factor of index k = c+1 along one axis: equilibrium, extended equilibrium, first-order dual
-  auto eqf = [&](int k, int a) { return k == 1 ? (R)1 - cs2 - ua2[a] : (R)0.5 * (cs2 + ua2[a] + (k == 2 ? uu[a] : -uu[a])); };
-  auto stf = [&](int k, int a) { return k == 1 ? (R)1 - zs[a] : (R)0.5 * (zs[a] + (k == 2 ? xs[a] : -xs[a])); };
-  auto d1f = [&](int k, int a) { return k == 1 ? (R)-2 * uu[a] : uu[a] + (k == 2 ? (R)0.5 : (R)-0.5); };
-  // x-axis factors, used for every population
-  R X[3], Xs[3], d1[3];
+  auto Ef = [&](int a, int k) { return k == 1 ? (R)1 - (R)2 * he[a] : (k == 0 ? he[a] - (R)0.5 * ua[a] : he[a] + (R)0.5 * ua[a]); };
+  auto Sf = [&](int a, int k) { return k == 1 ? (R)1 - (R)2 * hs[a] : (k == 0 ? hs[a] - (R)0.5 * xs[a] : hs[a] + (R)0.5 * xs[a]); };
+  auto Df = [&](int a, int k) { return k == 1 ? (R)-2 * ua[a] : (k == 0 ? ua[a] - (R)0.5 : ua[a] + (R)0.5); };
+  // x-axis factors, used by every population
+  R E[3], St[3], D1[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    X[k] = eqf(k, 0);
-    Xs[k] = stf(k, 0);
-    d1[k] = d1f(k, 0);
-  }
+  for (int k = 0; k < 3; ++k) { E[k] = Ef(0, k); St[k] = Sf(0, k); D1[k] = Df(0, k); }
   // second-order central Hermite moments; the shear part keeps the off-diagonals
   // and the deviatoric diagonal a_aa - trace/D
   const R axy = Pxy - rho * u[0] * u[1];
@@ -286,65 +430,93 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
   const R tr = (adx + ady + adz) * (R)(1.0 / D);
   const R devx = adx - tr, devy = ady - tr, devz = D == 3 ? adz - tr : (R)0;
 
-  // Row coefficients for the populations sharing (cy, cz): f^eq = ryz X_x, f* = rsyz Xs_x,
-  // s = d0_x C0 + d1_x C1 + d2_x C2 with d2 = {-1 at c = 0, 1/2 at c = +-1}.
-  struct Row { R ryz, rsyz, C0, C1, C2; };
-  auto row_coef = [&](int iy, int iz) {
-    const R Z0 = D == 3 ? eqf(iz, 2) : (R)1, Zs = D == 3 ? stf(iz, 2) : (R)1;
-    const R Z1 = D == 3 ? d1f(iz, 2) : (R)0;
-    const R Z2 = D == 3 ? (iz == 1 ? (R)-1 : (R)0.5) : (R)0;
-    const R Y0 = eqf(iy, 1), Y1 = d1f(iy, 1), Y2 = iy == 1 ? (R)-1 : (R)0.5;
-    Row r;
-    r.ryz = rho * Y0 * Z0;
-    r.rsyz = rho * stf(iy, 1) * Zs;
-    r.C0 = ayz * Y1 * Z1 + devy * Y2 * Z0 + (D == 3 ? devz * Y0 * Z2 : (R)0);
-    r.C1 = axy * Y1 * Z0 + (D == 3 ? axz * Y0 * Z1 : (R)0);
-    r.C2 = devx * Y0 * Z0;
-    return r;
-  };
-
-  // ---- pass A: entropic sums, h to shared memory, g = f - omega s + f* - f^eq
-  //      = h + (1 - omega) s + f* in place of f.  Every f*_i is positive exactly when
-  //      rho and the nine one-dimensional factors Xs are (each axis's three factors
-  //      sum to one, so they cannot all be negative).  The weight 1/f*_i factors as
-  //      1/(rho Ys Zs) times 1/Xs, so a row's three terms are summed with the x
-  //      reciprocals and scaled once by the row's; partial sums per iy keep the
-  //      dependency chains short.
+  // Every f*_i is positive exactly when rho and the one-dimensional factors St are
+  // (each axis's three factors sum to one, so they cannot all be negative).
   R fmin = rho;
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) fmin = fmin < stf(k, a) ? fmin : stf(k, a);
+    for (int k = 0; k < 3; ++k) fmin = fmin < Sf(a, k) ? fmin : Sf(a, k);
+
+  // ---- pass A: entropic sums, h to shared memory, g = f - omega s + f* - f^eq
+  //      = h + (1 - omega) s + f* in place of f.  A row (cy, cz) has f^eq = ryz E_x,
+  //      f* = rsyz St_x and s = E_x C0 + d1_x C1 + d2_x C2.  The weight 1/f*_i factors
+  //      as 1/rsyz times 1/St_x, so a row's three terms are summed with the x
+  //      reciprocals and scaled once by the row's.
   const R one_m_om = (R)1 - om;
-  R sAy[3] = {0, 0, 0}, sBy[3] = {0, 0, 0};
-  R iXs[3];
+  R iSt[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) iXs[k] = rcp_fast<R>(Xs[k]);
+  for (int k = 0; k < 3; ++k) iSt[k] = rcp_fast<R>(St[k]);
+  R2 SA = zero2, SB = zero2;
 #pragma unroll
-  for (int iz = 0; iz < (D == 3 ? 3 : 1); ++iz) {
-#pragma unroll
-    for (int iy = 0; iy < 3; ++iy) {
-      const Row r = row_coef(iy, iz);
-      R tA = 0, tB = 0;
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix) {
-        const int i = ix + 3 * iy + 9 * iz;
-        const R feq = r.ryz * X[ix];
-        const R fst = r.rsyz * Xs[ix];
-        const R s = X[ix] * r.C0 + d1[ix] * r.C1 + (ix == 1 ? -r.C2 : (R)0.5 * r.C2);
-        const R hh = f[i] - feq - s;
-        const R hr = hh * iXs[ix];
-        tA += s * hr;
-        tB += hh * hr;
-        s_h[i * NT + tid] = hh;
-        f[i] = hh + one_m_om * s + fst;
-      }
-      const R irs = rcp_fast<R>(r.rsyz);
-      sAy[iy] += irs * tA;
-      sBy[iy] += irs * tB;
+  for (int k = 0; k < NP; ++k) {
+    // row coefficients of the two lanes
+    R2 ryz, rsyz, C0, C1, C2;
+    if (k < NY) {
+      // lanes vary in y (cy = -1, +1); z fixed at cz = k - 1 (2-D: factors 1, 0, 0)
+      const R Z0 = D == 3 ? Ef(2, k) : (R)1, Zs = D == 3 ? Sf(2, k) : (R)1;
+      const R Z1 = D == 3 ? Df(2, k) : (R)0, Z2 = D == 3 ? (k == 1 ? (R)-1 : (R)0.5) : (R)0;
+      const R2 Y0 = two<R>(Ef(1, 0), Ef(1, 2)), Ys = two<R>(Sf(1, 0), Sf(1, 2)), Y1 = two<R>(Df(1, 0), Df(1, 2));
+      ryz = mul2(Y0, both<R>(rho * Z0));
+      rsyz = mul2(Ys, both<R>(rho * Zs));
+      C0 = fma2(Y1, both<R>(ayz * Z1), fma2(Y0, both<R>(devz * Z2), both<R>((R)0.5 * devy * Z0)));
+      C1 = fma2(Y1, both<R>(axy * Z0), mul2(Y0, both<R>(axz * Z1)));
+      C2 = mul2(Y0, both<R>(devx * Z0));
+    } else {
+      // lanes vary in z (cz = -1, +1); y fixed at cy = 0
+      const R Y0 = Ef(1, 1), Ys = Sf(1, 1), Y1 = Df(1, 1);
+      const R2 Z0 = two<R>(Ef(2, 0), Ef(2, 2)), Zs = two<R>(Sf(2, 0), Sf(2, 2)), Z1 = two<R>(Df(2, 0), Df(2, 2));
+      ryz = mul2(Z0, both<R>(rho * Y0));
+      rsyz = mul2(Zs, both<R>(rho * Ys));
+      C0 = fma2(Z1, both<R>(ayz * Y1), fma2(Z0, both<R>(-devy), both<R>((R)0.5 * devz * Y0)));
+      C1 = fma2(Z0, both<R>(axy * Y1), mul2(Z1, both<R>(axz * Y0)));
+      C2 = mul2(Z0, both<R>(devx * Y0));
     }
+    const R2 E0 = add2(ryz, C0);             // f^eq + (the X C0 part of s) = E_x (ryz + C0)
+    const R2 C2h = mul2(both<R>((R)0.5), C2);
+    R2 TA = zero2, TB = zero2;
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+      const R2 Xb = both<R>(E[ix]);
+      const R2 t = ix == 1 ? sub2(mul2(both<R>(D1[1]), C1), C2) : fma2(both<R>(D1[ix]), C1, C2h);
+      const R2 sv = fma2(Xb, C0, t);
+      const R2 hh = sub2(fp[k][ix], fma2(Xb, E0, t));
+      const R2 fst = mul2(rsyz, both<R>(St[ix]));
+      const R2 hr = mul2(hh, both<R>(iSt[ix]));
+      TA = fma2(sv, hr, TA);
+      TB = fma2(hh, hr, TB);
+      s_h2[(3 * k + ix) * NT + tid] = hh;
+      fp[k][ix] = fma2(both<R>(one_m_om), sv, add2(hh, fst));
+    }
+    const R2 irs = two<R>(rcp_fast<R>(rsyz.x), rcp_fast<R>(rsyz.y));
+    SA = fma2(irs, TA, SA);
+    SB = fma2(irs, TB, SB);
   }
-  const R sA = (sAy[0] + sAy[1]) + sAy[2], sB = (sBy[0] + sBy[1]) + sBy[2];
+  R sA, sB;
+  {
+    // the single row cy = cz = 0
+    const R Y0 = Ef(1, 1), Ys = Sf(1, 1), Y1 = Df(1, 1);
+    const R Z0 = D == 3 ? Ef(2, 1) : (R)1, Zs = D == 3 ? Sf(2, 1) : (R)1;
+    const R Z1 = D == 3 ? Df(2, 1) : (R)0, Z2 = D == 3 ? (R)-1 : (R)0;
+    const R ryz = rho * Y0 * Z0, rsyz = rho * Ys * Zs;
+    const R C0 = ayz * Y1 * Z1 - devy * Z0 + (D == 3 ? devz * Y0 * Z2 : (R)0);
+    const R C1 = axy * Y1 * Z0 + (D == 3 ? axz * Y0 * Z1 : (R)0);
+    const R C2 = devx * Y0 * Z0;
+    R tA = 0, tB = 0;
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+      const R sv = E[ix] * C0 + D1[ix] * C1 + (ix == 1 ? -C2 : (R)0.5 * C2);
+      const R hh = fs[ix] - ryz * E[ix] - sv;
+      const R hr = hh * iSt[ix];
+      tA += sv * hr;
+      tB += hh * hr;
+      s_h1[ix * NT + tid] = hh;
+      fs[ix] = hh + one_m_om * sv + rsyz * St[ix];
+    }
+    const R irs = rcp_fast<R>(rsyz);
+    sA = (SA.x + SA.y) + irs * tA;
+    sB = (SB.x + SB.y) + irs * tB;
+  }
 
   R gamma;
   if (d.gamma_mode == 1) {
@@ -359,41 +531,145 @@ __device__ __forceinline__ void collide_tile(const DevDomain& d, const CUtensorM
 
   // ---- pass B: f' = g - (omega gamma/2) h
   const R ch = (R)0.5 * om * gamma;
+  const R2 mch = both<R>(-ch);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] -= ch * s_h[i * NT + tid];
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) fp[k][ix] = fma2(mch, s_h2[(3 * k + ix) * NT + tid], fp[k][ix]);
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) fs[ix] -= ch * s_h1[ix * NT + tid];
 
   // ---- float16-deviation storage: encode against this node's density, which the
   //      next step reads back as the writer density of every slot written here
   if constexpr (DevStorage<S>::value) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = f[i] * (inv_rho * (R)(1.0 / wq<D>(i))) - (R)1;
+    for (int k = 0; k < NP; ++k)
+#pragma unroll
+      for (int ix = 0; ix < 3; ++ix)
+        fp[k][ix] = fma2(fp[k][ix], both<R>(inv_rho * (R)(1.0 / wq<D>(RP::pop(k, 0, ix)))), both<R>((R)-1));
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) fs[ix] = fs[ix] * (inv_rho * (R)(1.0 / wq<D>(RP::single(ix)))) - (R)1;
     d.rho_w[1 - P][n] = (float)rho;
   }
 
   // ---- stream: A-A write
-  S* Fo = (S*)d.f;
-  if (inner) {
+  const XBase xb = xbase(d, x, n);
+  auto store = [&](bool in) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_pop<S, R>(Fo + dst_slot<D, P>(d, true, x, y, z, n, i), f[i]);
-  } else {
+    for (int ix = 0; ix < 3; ++ix) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_pop<S, R>(Fo + dst_slot<D, P>(d, false, x, y, z, n, i), f[i]);
-  }
+      for (int k = 0; k < NP; ++k) {
+        st_pop<S, R>(dst_ptr<D, P, S>(d, in, xb, x, y, z, n, RP::pop(k, 0, ix)), fp[k][ix].x);
+        st_pop<S, R>(dst_ptr<D, P, S>(d, in, xb, x, y, z, n, RP::pop(k, 1, ix)), fp[k][ix].y);
+      }
+      st_pop<S, R>(dst_ptr<D, P, S>(d, in, xb, x, y, z, n, RP::single(ix)), fs[ix]);
+    }
+  };
+  if (fast) store(true);
+  else store(false);
+  return true;
 }
 
 template <int D, int P, typename S, typename R, typename A>
 __global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
-collide_stream_kernel(DevDomain d, const __grid_constant__ CUtensorMap aux_map) {
+collide_stream_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
-  __shared__ __align__(128) A s_aux[2 * Halo<D, BX, BY, BZ>::HN];  // [field][z][y][x]: rho, then s*psi
+  using H = Halo<D, BX, BY, BZ>;
+  __shared__ __align__(128) Two<A> s_aux[H::HN];                     // [z][y][x] (rho, psi)
+  __shared__ __align__(128) A s_q[D * H::template qstride<A>()];     // [a][z][y][x] q_a
   __shared__ __align__(8) unsigned long long tile_bar;
   // higher-order part h_i of every node of the tile, [i][thread] (dynamic: above 48 KB in float64)
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
   if (tid == 0) mbar_init(&tile_bar, 1);
   __syncthreads();
-  collide_tile<D, BX, BY, BZ, P, S, R, A, true>(d, &aux_map, blockIdx.x * BX, blockIdx.y * BY,
-                                                 D == 3 ? blockIdx.z * BZ : 0, s_aux, (R*)smem_dyn, &tile_bar, 0);
+  collide_tile<D, BX, BY, BZ, P, S, R, A, true>(d, &maps, blockIdx.x * BX, blockIdx.y * BY,
+                                                 D == 3 ? blockIdx.z * BZ : 0, s_aux, s_q, (R*)smem_dyn, &tile_bar, 0);
+}
+
+// Start the copies of the pre-collision populations of node (x, y, z) into the
+// staging buffer s_f ([i][thread]); nothing for a node outside the domain.
+template <int D, int P, typename S, int NT>
+__device__ __forceinline__ void stage_populations(const DevDomain& d, int x, int y, int z, S* s_f, int tid) {
+  constexpr int Q = Lattice<D>::Q;
+  if (!(x < d.nx && y < d.ny && z < d.nz)) return;
+  const long long n = node_of(d, x, y, z);
+  const XBase xb = xbase(d, x, n);
+  if (P == 0 || fast_links<D>(d, x, y, z)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) cp_async_word<sizeof(S)>(s_f + i * NT + tid, src_ptr<D, P, S>(d, true, xb, x, y, z, n, i));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) cp_async_word<sizeof(S)>(s_f + i * NT + tid, src_ptr<D, P, S>(d, false, xb, x, y, z, n, i));
+  }
+}
+
+// Persistent form of pass 2: a block walks the tiles t = blockIdx.x, + gridDim.x,
+// ... (x fastest).  While it computes tile t the copies of tile t + gridDim.x are in
+// flight: its populations (cp.async, started as soon as tile t's have been read
+// into registers; the A-A pattern makes that safe, since a node's read slots are
+// written by that node alone within the step) and, once the force stencil of tile t
+// is done, its halo tile (TMA).
+template <int D, int P, typename S, typename R, typename A>
+__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
+collide_stream_persistent_kernel(DevDomain d, const __grid_constant__ TileMaps maps, int ntx, int nty, int ntiles) {
+  constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
+  constexpr int NT = BX * BY * BZ;
+  using H = Halo<D, BX, BY, BZ>;
+  __shared__ __align__(128) Two<A> s_aux[H::HN];                  // [z][y][x] (rho, psi)
+  __shared__ __align__(128) A s_q[D * H::template qstride<A>()];  // [a][z][y][x] q_a
+  __shared__ __align__(8) unsigned long long tile_bar;
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  R* s_h = (R*)smem_dyn;                                            // [Q][NT] h
+  S* s_f = (S*)(smem_dyn + (size_t)Lattice<D>::Q * NT * sizeof(R));  // [Q][NT] staged populations
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  if (tid == 0) mbar_init(&tile_bar, 1);
+  __syncthreads();
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  auto origin = [&](int tt, int& ox, int& oy, int& oz) {
+    ox = (tt % ntx) * BX;
+    oy = ((tt / ntx) % nty) * BY;
+    oz = D == 3 ? (tt / (ntx * nty)) * BZ : 0;
+  };
+  int x0, y0, z0;
+  origin(t, x0, y0, z0);
+  stage_populations<D, P, S, NT>(d, x0 + threadIdx.x, y0 + threadIdx.y, z0 + threadIdx.z, s_f, tid);
+  cp_async_commit();
+  if (tid == 0) tma_load_fields<D, BX, BY, BZ, A>(&maps, s_aux, s_q, &tile_bar, x0, y0, z0);
+  for (uint32_t it = 0;; ++it) {
+    const int tn = t + (int)gridDim.x;
+    int nx0 = 0, ny0 = 0, nz0 = 0;
+    if (tn < ntiles) origin(tn, nx0, ny0, nz0);
+    struct Next {
+      const DevDomain& d;
+      const TileMaps* maps;
+      Two<A>* s_aux;
+      A* s_q;
+      unsigned long long* bar;
+      S* s_f;
+      int tid, x0, y0, z0;
+      bool valid;
+      __device__ void prefetch() const {
+        if (valid) stage_populations<D, P, S, NT>(d, x0 + threadIdx.x, y0 + threadIdx.y, z0 + threadIdx.z, s_f, tid);
+        cp_async_commit();
+      }
+      __device__ void aux() const {
+        if (valid && tid == 0) {
+          fence_proxy_async_smem();
+          tma_load_fields<D, BX, BY, BZ, A>(maps, s_aux, s_q, bar, x0, y0, z0);
+        }
+      }
+    } next{d, &maps, s_aux, s_q, &tile_bar, s_f, tid, nx0, ny0, nz0, tn < ntiles};
+    cp_async_wait_all();  // this thread's populations of tile t are in s_f
+    if (!collide_tile<D, BX, BY, BZ, P, S, R, A, true, true, Next>(d, &maps, x0, y0, z0, s_aux, s_q, s_h, &tile_bar,
+                                                                     it & 1u, s_f, next))
+      break;
+    if (tn >= ntiles) break;
+    t = tn;
+    x0 = nx0; y0 = ny0; z0 = nz0;
+  }
+  cp_async_wait_all();  // no copy of this block still in flight at exit
 }
 
 }  // namespace lbm

@@ -3,14 +3,16 @@
 //
 // Data layout in HBM (one domain):
 //   populations  f[i * N + node]          SoA, node = x + nx*(y + ny*z), one A-A buffer
-//   auxiliary    aux[field * PN + pnode]  fields rho, s*psi, q_x, q_y(, q_z); padded by a
-//                                         2-node ghost layer on every axis (2-D: z not padded)
+//   auxiliary    aux2[pnode] = (rho, psi) interleaved pairs, then q_a[pnode] planes
+//                                         (element offset (2 + a) * PN); padded by a 2-node
+//                                         ghost layer on every axis (2-D: z not padded)
 // The A-A pattern keeps one population buffer: an even step (parity 0) reads and
 // writes the node's own slots (writing direction i into slot Q-1-i), an odd step
 // (parity 1) reads the neighbours' slots and writes back into them, so that after
 // each odd step slot i of node r holds f_i(r) again.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -46,7 +48,35 @@ template <typename R> struct Phys {
   R RT, b, aalpha;               // Peng-Robinson: P = rho RT/(1 - b rho) - aalpha rho^2/(1 + 2 b rho - b^2 rho^2)
   R gamma_value;
   R band_lo, band_hi;            // interface band of densities (float64 EOS inside it when eos_fp64 == 1)
+  // Sign s of P(rho) - rho cs^2: sgn0 below every threshold, flipped once for every
+  // threshold t <= rho.  The thresholds are the smallest values of R above the roots
+  // of P(rho) = rho cs^2 on (0, 1/b) (at most three), +inf where unused.
+  R sgn_t[3];
+  R sgn0;
 };
+
+// ---- two lanes of the arithmetic type ----
+// float32 pairs are one packed FFMA2/FADD2/FMUL2 instruction for both lanes
+// (round to nearest, each lane exactly the scalar operation); float64 pairs are
+// two scalar operations.
+template <typename R> struct TwoOf;
+template <> struct TwoOf<float> { using T = float2; };
+template <> struct TwoOf<double> { using T = double2; };
+template <typename R> using Two = typename TwoOf<R>::T;
+
+template <typename R> __device__ __forceinline__ Two<R> two(R a, R b) { return Two<R>{a, b}; }
+template <typename R> __device__ __forceinline__ Two<R> both(R a) { return Two<R>{a, a}; }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, exact as a subtraction (b * -1 is exact, one rounding)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return double2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return double2{a.x * b.x, a.y * b.y}; }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return double2{fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)};
+}
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return double2{a.x - b.x, a.y - b.y}; }
 
 // ---- what a kernel needs to know about a domain (passed by value) ----
 struct DevDomain {
@@ -63,11 +93,12 @@ struct DevDomain {
   int eos_fp64;
   Phys<double> pd;     // parameters for the float64 path and the float64 islands
   Phys<float> pf;      // the same rounded to float32
-  // Element offsets, relative to node r's own slot 0, of the slot population i
-  // is read from (src) and written to (dst) at an interior node, per A-A parity:
-  // src[0][i] = i N, src[1][i] = (Q-1-i) N - off(c_i); dst[0][i] = (Q-1-i) N,
-  // dst[1][i] = i N + off(c_i), off(c) = cx + nx cy + nx ny cz.
-  long long src_off[2][27], dst_off[2][27];
+  // Byte offsets, relative to node r's own slot 0, of the slot population i is
+  // read from (src) and written to (dst) at an interior node, per A-A parity, in
+  // elements: src[0][i] = i N, src[1][i] = (Q-1-i) N - off(c_i); dst[0][i] = (Q-1-i) N,
+  // dst[1][i] = i N + off(c_i), off(c) = cx + nx cy + nx ny cz; times the size of a
+  // stored population.
+  long long src_boff[2][27], dst_boff[2][27];
   // Element offset of the upstream node r - c_i of an interior node: the node that
   // wrote the slot population i of r is read from, in either parity.
   long long up_off[27];
@@ -75,6 +106,12 @@ struct DevDomain {
   // parity (a step of parity P decodes with rho_w[P] and records its own
   // densities in rho_w[1 - P]); nullptr otherwise.
   float* rho_w[2];
+};
+
+// The tensor maps of the collide kernel's TMA loads (passed as a kernel parameter).
+struct TileMaps {
+  CUtensorMap aux;  // (rho, psi) halo tile
+  CUtensorMap q;    // q_a boxes
 };
 
 // float16-deviation storage: a slot holds delta = f/(w_i rho_w) - 1 in half
@@ -92,6 +129,10 @@ template <typename S, typename R> __device__ __forceinline__ void st_pop(S* p, R
 template <> __device__ __forceinline__ float ld_pop<__half, float>(const __half* p) { return __half2float(*p); }
 template <> __device__ __forceinline__ double ld_pop<__half, double>(const __half* p) { return (double)__half2float(*p); }
 template <> __device__ __forceinline__ void st_pop<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
+// Post-collision populations are not read again within the step: streaming
+// (evict-first) stores keep the auxiliary fields in L2 instead.
+template <> __device__ __forceinline__ void st_pop<float, float>(float* p, float v) { __stcs(p, v); }
+template <> __device__ __forceinline__ void st_pop<double, double>(double* p, double v) { __stcs(p, v); }
 
 __device__ __forceinline__ long long node_of(const DevDomain& d, int x, int y, int z) {
   return (long long)x + (long long)d.nx * ((long long)y + (long long)d.ny * (long long)z);
@@ -101,10 +142,25 @@ __device__ __forceinline__ long long pnode_of(const DevDomain& d, int x, int y, 
   return (long long)(x + 2) + (long long)d.px * ((long long)(y + 2) + (long long)d.py * (long long)(D == 3 ? z + 2 : 0));
 }
 
-// A node whose every lattice link stays inside the domain (no wrap, no wall).
+// A node whose links leave the domain only across a periodic x boundary: every
+// y and z neighbour inside, every x neighbour inside or wrapped periodically.  The
+// lanes of a warp share y and z (a warp is one x row), so with periodic x they all
+// take the same path.
 template <int D>
-__device__ __forceinline__ bool interior(const DevDomain& d, int x, int y, int z) {
-  return x >= 1 && x <= d.nx - 2 && y >= 1 && y <= d.ny - 2 && (D == 2 || (z >= 1 && z <= d.nz - 2));
+__device__ __forceinline__ bool fast_links(const DevDomain& d, int x, int y, int z) {
+  return y >= 1 && y <= d.ny - 2 && (D == 2 || (z >= 1 && z <= d.nz - 2)) &&
+         ((x >= 1 && x <= d.nx - 2) || (d.wall_lo[0] == 0 && d.wall_hi[0] == 0));
+}
+
+// Node index n of (x, y, z) corrected for the periodic x wrap of the neighbour
+// r - c along x: b[c + 1], c = -1, 0, +1 (used by fast_links nodes only).
+struct XBase { long long b[3]; };
+__device__ __forceinline__ XBase xbase(const DevDomain& d, int x, long long n) {
+  XBase r;
+  r.b[0] = x == d.nx - 1 ? n - d.nx : n;  // x + 1 wraps to 0
+  r.b[1] = n;
+  r.b[2] = x == 0 ? n + d.nx : n;         // x - 1 wraps to nx - 1
+  return r;
 }
 
 // Neighbour coordinate along one axis: periodic wrap, or wall = true when the
@@ -119,36 +175,43 @@ __device__ __forceinline__ int step_axis(int x, int c, int n, int wlo, int whi, 
 // Slot holding the pre-collision population i of node (x,y,z) at parity P:
 // P = 0: slot i of the node; P = 1: slot Q-1-i of the upstream node r - c_i, or
 // slot i of the node itself when the upstream link crosses a wall.
-template <int D, int P>
-__device__ __forceinline__ long long src_slot(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
+template <int D, int P, typename S>
+__device__ __forceinline__ S* src_ptr(const DevDomain& d, bool fast, const XBase& xb, int x, int y, int z, long long n,
+                                      int i) {
   constexpr int Q = Lattice<D>::Q;
-  if (P == 0 || inner) return n + d.src_off[P][i];
+  S* F = (S*)d.f;
+  if (P == 0) return (S*)((char*)(F + n) + d.src_boff[0][i]);
+  if (fast) return (S*)((char*)(F + xb.b[cxi(i) + 1]) + d.src_boff[1][i]);
   bool wall = false;
   const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
   const int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-  return wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz);
+  return F + (wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz));
 }
 
 // Slot receiving the post-collision population i of node (x,y,z) at parity P:
 // streaming f_i(r + c_i) <- f'_i(r); half-way bounce-back f_{Q-1-i}(r) <- f'_i(r)
 // when r + c_i lies beyond a wall.
-template <int D, int P>
-__device__ __forceinline__ long long dst_slot(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
+template <int D, int P, typename S>
+__device__ __forceinline__ S* dst_ptr(const DevDomain& d, bool fast, const XBase& xb, int x, int y, int z, long long n,
+                                      int i) {
   constexpr int Q = Lattice<D>::Q;
-  if (P == 0 || inner) return n + d.dst_off[P][i];
+  S* F = (S*)d.f;
+  if (P == 0) return (S*)((char*)(F + n) + d.dst_boff[0][i]);
+  if (fast) return (S*)((char*)(F + xb.b[1 - cxi(i)]) + d.dst_boff[1][i]);
   bool wall = false;
   const int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
   const int tz = D == 3 ? step_axis(z, czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-  return wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz);
+  return F + (wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz));
 }
 
 // Node that wrote the slot population i of node (x,y,z) is read from: the
 // upstream node r - c_i, or the node itself when that link crosses a wall.
 template <int D>
-__device__ __forceinline__ long long upstream_node(const DevDomain& d, bool inner, int x, int y, int z, long long n, int i) {
-  if (inner) return n + d.up_off[i];
+__device__ __forceinline__ long long upstream_node(const DevDomain& d, bool fast, const XBase& xb, int x, int y, int z,
+                                                   long long n, int i) {
+  if (fast) return xb.b[cxi(i) + 1] + d.up_off[i];
   bool wall = false;
   const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
@@ -159,30 +222,28 @@ __device__ __forceinline__ long long upstream_node(const DevDomain& d, bool inne
 template <int D, int P, typename S, typename R>
 __device__ __forceinline__ void gather(const DevDomain& d, int x, int y, int z, R* f) {
   constexpr int Q = Lattice<D>::Q;
-  const S* F = (const S*)d.f;
   const long long n = node_of(d, x, y, z);
+  const XBase xb = xbase(d, x, n);
   if constexpr (DevStorage<S>::value) {
     // f_i = w_i rho_w (1 + delta_i)
     const float* rw = d.rho_w[P];
-    if (interior<D>(d, x, y, z)) {
+    if (fast_links<D>(d, x, y, z)) {
 #pragma unroll
       for (int i = 0; i < Q; ++i)
-        f[i] = (R)wq<D>(i) * (R)rw[upstream_node<D>(d, true, x, y, z, n, i)] *
-               ((R)1 + ld_pop<S, R>(F + src_slot<D, P>(d, true, x, y, z, n, i)));
+        f[i] = (R)wq<D>(i) * (R)rw[upstream_node<D>(d, true, xb, x, y, z, n, i)] *
+               ((R)1 + ld_pop<S, R>(src_ptr<D, P, S>(d, true, xb, x, y, z, n, i)));
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i)
-        f[i] = (R)wq<D>(i) * (R)rw[upstream_node<D>(d, false, x, y, z, n, i)] *
-               ((R)1 + ld_pop<S, R>(F + src_slot<D, P>(d, false, x, y, z, n, i)));
+        f[i] = (R)wq<D>(i) * (R)rw[upstream_node<D>(d, false, xb, x, y, z, n, i)] *
+               ((R)1 + ld_pop<S, R>(src_ptr<D, P, S>(d, false, xb, x, y, z, n, i)));
     }
+  } else if (P == 0 || fast_links<D>(d, x, y, z)) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(src_ptr<D, P, S>(d, true, xb, x, y, z, n, i));
   } else {
-    if (interior<D>(d, x, y, z)) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, true, x, y, z, n, i));
-    } else {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(F + src_slot<D, P>(d, false, x, y, z, n, i));
-    }
+    for (int i = 0; i < Q; ++i) f[i] = ld_pop<S, R>(src_ptr<D, P, S>(d, false, xb, x, y, z, n, i));
   }
 }
 
@@ -226,21 +287,27 @@ __device__ __forceinline__ T pr_pressure(const Phys<T>& p, T rho) {
   return rho * p.RT / ((T)1 - p.b * rho) - p.aalpha * rho * rho / ((T)1 + (T)2 * p.b * rho - p.b * p.b * rho * rho);
 }
 
-// Signed pseudo-potential s*psi, psi = sqrt|P - P0|, s = +1 if P > P0 else -1 (Sec. 2.3).
-// The sign travels in the sign bit (-0 when P == P0).
+// Pseudo-potential psi = sqrt|P - P0|, P0 = rho cs^2 (Sec. 2.3); its sign s comes
+// from psi_sign.
 template <typename R>
-__device__ __forceinline__ R signed_psi(const DevDomain& d, R rho) {
+__device__ __forceinline__ R psi_of(const DevDomain& d, R rho) {
   if (sizeof(R) == 8 || d.eos_fp64 == 2 ||
       (d.eos_fp64 == 1 && rho > phys<R>(d).band_lo && rho < phys<R>(d).band_hi)) {
     const double r = (double)rho;
-    const double dd = pr_pressure<double>(d.pd, r) - r * (1.0 / 3.0);
-    const double ps = sqrt(fabs(dd));
-    return (R)(dd > 0.0 ? ps : -ps);
+    return (R)sqrt(fabs(pr_pressure<double>(d.pd, r) - r * (1.0 / 3.0)));
   }
   const float r = (float)rho;
-  const float df = pr_pressure<float>(d.pf, r) - r * (1.0f / 3.0f);
-  const float ps = sqrtf(fabsf(df));
-  return (R)(df > 0.0f ? ps : -ps);
+  return (R)sqrtf(fabsf(pr_pressure<float>(d.pf, r) - r * (1.0f / 3.0f)));
+}
+
+// s = +1 where P(rho) > rho cs^2, else -1 (Sec. 2.3), from the host-computed
+// densities where P(rho) - rho cs^2 changes sign.
+template <typename R>
+__device__ __forceinline__ R psi_sign(const Phys<R>& p, R rho) {
+  R s = p.sgn0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s = rho >= p.sgn_t[k] ? -s : s;
+  return s;
 }
 
 template <typename R>

@@ -11,7 +11,7 @@
 #include "lbm_ops.h"
 
 struct lbm_domain {
-  alignas(64) CUtensorMap aux_map;  // rho and s*psi halo tiles for the collide kernel's TMA load
+  lbm::TileMaps maps;  // halo tiles of (rho, psi) and q for the collide kernel's TMA loads
   lbm_params p{};
   const lbm::Ops* ops = nullptr;
   lbm::DevDomain dev{};

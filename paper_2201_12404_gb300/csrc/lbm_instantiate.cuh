@@ -19,12 +19,54 @@ struct Launch {
     if (parity == 0) moments_eos_kernel<D, 0, S, R, A><<<grd, blk, 0, s>>>(d);
     else moments_eos_kernel<D, 1, S, R, A><<<grd, blk, 0, s>>>(d);
   }
-  static void collide_stream(const DevDomain& d, const CUtensorMap& map, int parity, cudaStream_t s) {
+  static void collide_stream(const DevDomain& d, const TileMaps& maps, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
-    constexpr size_t smem = collide_dyn_smem<D, R>();
-    auto k = parity == 0 ? collide_stream_kernel<D, 0, S, R, A> : collide_stream_kernel<D, 1, S, R, A>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<node_grid(d), blk, smem, s>>>(d, map);
+    if constexpr (sizeof(S) == 8) {
+      // float64: one block per SM, so the persistent form keeps the next tile's
+      // loads in flight; float32 and float16 keep one tile per block (three blocks
+      // per SM overlap each other's loads, and the staging copies would only add
+      // shared-memory traffic)
+      constexpr size_t smem = persistent_dyn_smem<D, S, R>();
+      auto k = parity == 0 ? collide_stream_persistent_kernel<D, 0, S, R, A>
+                           : collide_stream_persistent_kernel<D, 1, S, R, A>;
+      const dim3 tiles = node_grid(d);
+      const long long ntiles = (long long)tiles.x * tiles.y * tiles.z;
+      const int slots = resident_slots((const void*)k, blk.x * blk.y * blk.z, smem);
+      const int grid = (int)(ntiles < slots ? ntiles : slots);
+      k<<<grid, blk, smem, s>>>(d, maps, (int)tiles.x, (int)tiles.y, (int)ntiles);
+    } else {
+      constexpr size_t smem = collide_dyn_smem<D, R>();
+      auto k = parity == 0 ? collide_stream_kernel<D, 0, S, R, A> : collide_stream_kernel<D, 1, S, R, A>;
+      // static (staged fields) plus dynamic (h) shared memory exceeds the 48 KB default
+      constexpr int kMaxDev = 64;
+      static bool opted_in[2][kMaxDev] = {};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= kMaxDev || !opted_in[parity][dev]) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (dev >= 0 && dev < kMaxDev) opted_in[parity][dev] = true;
+      }
+      k<<<node_grid(d), blk, smem, s>>>(d, maps);
+    }
+  }
+  // Blocks of kernel k resident on the whole device at once (SMs x blocks per SM),
+  // with the dynamic shared memory attributes set; computed once per kernel and device.
+  static int resident_slots(const void* k, int threads, size_t smem) {
+    constexpr int kMaxDev = 64;
+    static int cache[2][kMaxDev] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int which = k == (const void*)collide_stream_persistent_kernel<D, 0, S, R, A> ? 0 : 1;
+    int* slot = dev >= 0 && dev < kMaxDev ? &cache[which][dev] : nullptr;
+    if (slot && *slot > 0) return *slot;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int n = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (slot) *slot = n;
+    return n;
   }
   static unsigned blocks1d(const DevDomain& d) { return (unsigned)((d.N + 255) / 256); }
   static void init_equilibrium(const DevDomain& d, const double* rho, const double* ux, const double* uy,

@@ -42,8 +42,7 @@ __device__ __forceinline__ void moments_eos_node(const DevDomain& d, int xp, int
 
   A* aux = (A*)d.aux;
   const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * (long long)zp);
-  aux[pn] = (A)rho;
-  aux[d.PN + pn] = (A)signed_psi<R>(d, rho);
+  ((Two<A>*)aux)[pn] = two<A>((A)rho, (A)psi_of<R>(d, rho));
   // q_a = rho u_a (u_a^2 + 3 P0/rho - 3 cs^2) = rho u_a^3 since P0/rho = cs^2
   const R inv = (R)1 / rho;
 #pragma unroll
@@ -89,11 +88,12 @@ __global__ void init_equilibrium_kernel(DevDomain d, const double* rho, const do
     // each slot is encoded against the density of its upstream (writer) node; the
     // next step (even parity) decodes with rho_w[0] of that node
     const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
-    const bool inner = interior<D>(d, x, y, z);
+    const bool fast = fast_links<D>(d, x, y, z);
+    const XBase xb = xbase(d, x, n);
     d.rho_w[0][n] = (float)r;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double rw = (double)(float)rho[upstream_node<D>(d, inner, x, y, z, n, i)];
+      const double rw = (double)(float)rho[upstream_node<D>(d, fast, xb, x, y, z, n, i)];
       const double feq = r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1];
       F[(long long)i * d.N + n] = __float2half_rn((float)(feq / (wq<D>(i) * rw) - 1.0));
     }
@@ -127,9 +127,10 @@ __global__ void canonical_write_kernel(DevDomain d, const double* in) {
   if constexpr (DevStorage<S>::value) {
     // rho_w[0] holds every node's density (canonical_density_kernel, launched before)
     const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
-    const bool inner = interior<D>(d, x, y, z);
+    const bool fast = fast_links<D>(d, x, y, z);
+    const XBase xb = xbase(d, x, n);
     for (int i = 0; i < Q; ++i) {
-      const double rw = (double)d.rho_w[0][upstream_node<D>(d, inner, x, y, z, n, i)];
+      const double rw = (double)d.rho_w[0][upstream_node<D>(d, fast, xb, x, y, z, n, i)];
       F[(long long)i * d.N + n] = __float2half_rn((float)(in[(long long)i * d.N + n] / (wq<D>(i) * rw) - 1.0));
     }
   } else {
@@ -162,16 +163,15 @@ __global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, dou
   gather<D, S, R>(d, parity, x, y, z, f);
   R rho, j[3], Pi[6];
   moments<D, R>(f, rho, j, Pi);
-  const A* a_rho = (const A*)d.aux;
-  const A* a_psi = a_rho + d.PN;
+  const Two<A>* a2 = (const Two<A>*)d.aux;  // (rho, psi)
   const long long pc = pnode_of<D>(d, x, y, z);
   const long long sy = d.px, sz = (long long)d.px * d.py;
   R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
   for (int i = 0; i < Q; ++i) {
     if (i == Lattice<D>::REST) continue;
     const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
-    const R t4 = (R)(4.0 / 3.0) * fabs((R)a_psi[pc + o]) - (R)(1.0 / 6.0) * fabs((R)a_psi[pc + 2 * o]);
-    const R t3 = (R)2 * (R)a_rho[pc + o] - (R)a_rho[pc + 2 * o];
+    const R t4 = (R)(4.0 / 3.0) * (R)a2[pc + o].y - (R)(1.0 / 6.0) * (R)a2[pc + 2 * o].y;
+    const R t3 = (R)2 * (R)a2[pc + o].x - (R)a2[pc + 2 * o].x;
     const R W = (R)(3.0 * wq<D>(i));
     for (int a = 0; a < D; ++a) {
       const int c = cq<D>(i, a);
@@ -180,8 +180,9 @@ __global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, dou
     }
   }
   rho_out[n] = (double)rho;
+  const R spsi_c = psi_sign<R>(phys<R>(d), (R)a2[pc].x) * (R)a2[pc].y;
   for (int a = 0; a < D; ++a) {
-    const R Fa = -((R)2 * (R)a_psi[pc] * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
+    const R Fa = -((R)2 * spsi_c * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
     u_out[a * d.N + n] = (double)((j[a] + (R)0.5 * Fa) / rho);
   }
 }
@@ -196,16 +197,15 @@ __global__ void bare_velocity_kernel(DevDomain d, const double* rho_in, double* 
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.N) return;
   const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
-  const A* a_rho = (const A*)d.aux;
-  const A* a_psi = a_rho + d.PN;
+  const Two<A>* a2 = (const Two<A>*)d.aux;  // (rho, psi)
   const long long pc = pnode_of<D>(d, x, y, z);
   const long long sy = d.px, sz = (long long)d.px * d.py;
   R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
   for (int i = 0; i < Q; ++i) {
     if (i == Lattice<D>::REST) continue;
     const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
-    const R t4 = (R)(4.0 / 3.0) * fabs((R)a_psi[pc + o]) - (R)(1.0 / 6.0) * fabs((R)a_psi[pc + 2 * o]);
-    const R t3 = (R)2 * (R)a_rho[pc + o] - (R)a_rho[pc + 2 * o];
+    const R t4 = (R)(4.0 / 3.0) * (R)a2[pc + o].y - (R)(1.0 / 6.0) * (R)a2[pc + 2 * o].y;
+    const R t3 = (R)2 * (R)a2[pc + o].x - (R)a2[pc + 2 * o].x;
     const R W = (R)(3.0 * wq<D>(i));
     for (int a = 0; a < D; ++a) {
       const int c = cq<D>(i, a);
@@ -213,9 +213,10 @@ __global__ void bare_velocity_kernel(DevDomain d, const double* rho_in, double* 
       g3[a] += W * (R)c * t3;
     }
   }
-  const R rho = (R)a_rho[pc];
+  const R rho = (R)a2[pc].x;
+  const R spsi_c = psi_sign<R>(phys<R>(d), rho) * (R)a2[pc].y;
   for (int a = 0; a < D; ++a) {
-    const R Fa = -((R)2 * (R)a_psi[pc] * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
+    const R Fa = -((R)2 * spsi_c * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
     u[a * d.N + n] -= (double)Fa / (2.0 * rho_in[n]);
   }
 }

@@ -13,6 +13,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_ops.h"
+#include "lbm_phys.h"
 
 namespace {
 
@@ -68,33 +69,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
     d.wall_lo[a] = a < D && p->bc[2 * a] == LBM_BC_BOUNCEBACK;
     d.wall_hi[a] = a < D && p->bc[2 * a + 1] == LBM_BC_BOUNCEBACK;
   }
-  lbm::Phys<double>& pd = d.pd;
-  pd.kappa = p->kappa;
-  for (int a = 0; a < 3; ++a) pd.g[a] = a < D ? p->body_force[a] : 0.0;
-  pd.nu_v = p->nu_vapour;
-  pd.dnu = p->nu_liquid - p->nu_vapour;
-  pd.rho_v = p->rho_vapour;
-  pd.inv_drho = 1.0 / (p->rho_liquid - p->rho_vapour);
-  const double Tc = 0.0778 * p->a / (0.45724 * p->b * p->R);
-  const double m = 0.37464 + 1.54226 * p->acentric - 0.26992 * p->acentric * p->acentric;
-  const double sq = 1.0 + m * (1.0 - std::sqrt(p->T_over_Tc));
-  pd.RT = p->R * p->T_over_Tc * Tc;
-  pd.b = p->b;
-  pd.aalpha = p->a * sq * sq;
-  pd.gamma_value = p->gamma_value;
-  const double span = p->rho_liquid - p->rho_vapour;
-  pd.band_lo = p->rho_vapour + 0.01 * span;
-  pd.band_hi = p->rho_liquid - 0.01 * span;
-  lbm::Phys<float>& pf = d.pf;
-  pf.kappa = (float)pd.kappa;
-  for (int a = 0; a < 3; ++a) pf.g[a] = (float)pd.g[a];
-  pf.nu_v = (float)pd.nu_v; pf.dnu = (float)pd.dnu; pf.rho_v = (float)pd.rho_v; pf.inv_drho = (float)pd.inv_drho;
-  pf.RT = (float)pd.RT; pf.b = (float)pd.b; pf.aalpha = (float)pd.aalpha;
-  pf.gamma_value = (float)pd.gamma_value;
-  pf.band_lo = (float)pd.band_lo; pf.band_hi = (float)pd.band_hi;
-  d.gamma_mode = p->gamma_mode;
-  d.eos_fp64 = p->eos_fp64;
-  lbm::fill_slot_offsets(d, D);
+  lbm::fill_phys(d, *p, D);
+  lbm::fill_slot_offsets(d, D, ops->pop_bytes);
 
   unsigned char* scratch = nullptr;
   lbm_status st = scratch_address(&scratch);
@@ -105,9 +81,9 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   d.aux = scratch + kHeaderBytes;
   d.gamma_out = nullptr;
 
-  alignas(64) CUtensorMap aux_map;
+  lbm::TileMaps maps;
   const char* why = nullptr;
-  if (!lbm::make_aux_map(&aux_map, d, D, ops->aux_bytes, &why)) return LBM_ERR_CUDA;
+  if (!lbm::make_tile_maps(&maps, d, D, ops->aux_bytes, &why)) return LBM_ERR_CUDA;
 
   cudaStream_t stream = (cudaStream_t)p->stream;
   // the scratch keeps the previous call's contents: clear the flags and the counter
@@ -115,7 +91,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   int parity = 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     ops->moments_eos(d, parity, stream);
-    ops->collide_stream(d, aux_map, parity, stream);
+    ops->collide_stream(d, maps, parity, stream);
     parity ^= 1;
   }
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

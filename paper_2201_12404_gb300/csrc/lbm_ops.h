@@ -13,7 +13,7 @@ struct Ops {
   size_t pop_bytes;  // bytes per stored population
   size_t aux_bytes;  // bytes per auxiliary value
   void (*moments_eos)(const DevDomain&, int parity, cudaStream_t);
-  void (*collide_stream)(const DevDomain&, const CUtensorMap& aux_map, int parity, cudaStream_t);
+  void (*collide_stream)(const DevDomain&, const TileMaps& maps, int parity, cudaStream_t);
   void (*init_equilibrium)(const DevDomain&, const double* rho, const double* ux, const double* uy,
                            const double* uz, cudaStream_t);
   void (*canonical_read)(const DevDomain&, int parity, double* out, cudaStream_t);
@@ -29,16 +29,18 @@ struct Ops {
 extern const Ops ops_d2q9_fp64, ops_d2q9_fp32, ops_d3q27_fp64, ops_d3q27_fp32;
 extern const Ops ops_d2q9_fp16dev, ops_d3q27_fp16dev;
 
-// Fill the interior-node slot offset tables of d (needs d.N, d.nx, d.ny set).
-inline void fill_slot_offsets(DevDomain& d, int D) {
+// Fill the interior-node slot offset tables of d (needs d.N, d.nx, d.ny set) for
+// populations stored in elem_bytes bytes.
+inline void fill_slot_offsets(DevDomain& d, int D, size_t elem_bytes) {
   const int Q = D == 3 ? 27 : 9;
+  const long long e = (long long)elem_bytes;
   for (int i = 0; i < 27; ++i) {
     const long long off = (long long)cxi(i) + (long long)d.nx * cyi(i) + (D == 3 ? (long long)d.nx * d.ny * czi(i) : 0ll);
     const bool live = i < Q;
-    d.src_off[0][i] = live ? (long long)i * d.N : 0;
-    d.src_off[1][i] = live ? (long long)(Q - 1 - i) * d.N - off : 0;
-    d.dst_off[0][i] = live ? (long long)(Q - 1 - i) * d.N : 0;
-    d.dst_off[1][i] = live ? (long long)i * d.N + off : 0;
+    d.src_boff[0][i] = live ? e * ((long long)i * d.N) : 0;
+    d.src_boff[1][i] = live ? e * ((long long)(Q - 1 - i) * d.N - off) : 0;
+    d.dst_boff[0][i] = live ? e * ((long long)(Q - 1 - i) * d.N) : 0;
+    d.dst_boff[1][i] = live ? e * ((long long)i * d.N + off) : 0;
     d.up_off[i] = live ? -off : 0;
   }
 }
@@ -48,42 +50,56 @@ inline void fill_slot_offsets(DevDomain& d, int D) {
 // (a tensor-map stride requirement); the extra columns are never read.
 inline int padded_x(int nx) { return (nx + 4 + 3) / 4 * 4; }
 
-// Tensor map over the first two auxiliary fields (rho, s*psi) of d: a
-// (px, py[, pz], 2) tensor of float32 or float64 with a box of one halo tile,
-// (Blocks::bx + 4, Blocks::by + 4[, Blocks::bz + 4], 2).  Returns false with a
-// message when the driver refuses it.
-inline bool make_aux_map(CUtensorMap* map, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
-  typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static encode_fn encode = nullptr;
+// cuTensorMapEncodeTiled from the driver (no link against libcuda).
+typedef CUresult (*tensor_map_encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                         const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                         CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline tensor_map_encode_fn tensor_map_encoder(const char** why) {
+  static tensor_map_encode_fn encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn) {
       *why = "cuTensorMapEncodeTiled is not available from the driver";
-      return false;
+      return nullptr;
     }
-    encode = (encode_fn)fn;
+    encode = (tensor_map_encode_fn)fn;
   }
-  const CUtensorMapDataType type = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return encode;
+}
+
+// Tensor map over the interleaved (rho, psi) pairs at the start of d.aux, with a
+// box of one halo tile (Blocks::bx + 4, Blocks::by + 4[, Blocks::bz + 4]) of pairs.
+// float32 pairs are single 8-byte elements of a (px, py[, pz]) tensor; float64
+// pairs are the 16-byte innermost dimension of a (2, px, py[, pz]) tensor (a box's
+// innermost extent must be a multiple of 16 bytes).  Returns false with a message
+// when the driver refuses it.
+inline bool make_aux_map(CUtensorMap* map, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
+  const tensor_map_encode_fn encode = tensor_map_encoder(why);
+  if (!encode) return false;
+  const size_t pair_bytes = 2 * elem_bytes;
+  const cuuint64_t ext[3] = {(cuuint64_t)d.px, (cuuint64_t)d.py, (cuuint64_t)d.pz};
+  const cuuint32_t tile[3] = {D == 3 ? (cuuint32_t)Blocks<3>::bx + 4 : (cuuint32_t)Blocks<2>::bx + 4,
+                              D == 3 ? (cuuint32_t)Blocks<3>::by + 4 : (cuuint32_t)Blocks<2>::by + 4,
+                              (cuuint32_t)Blocks<3>::bz + 4};
   cuuint64_t dims[4], strides[3];
   cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
-  cuuint32_t rank;
-  if (D == 3) {
-    rank = 4;
-    dims[0] = d.px; dims[1] = d.py; dims[2] = d.pz; dims[3] = 2;
-    strides[0] = (cuuint64_t)d.px * elem_bytes;
-    strides[1] = (cuuint64_t)d.px * d.py * elem_bytes;
-    strides[2] = (cuuint64_t)d.PN * elem_bytes;
-    box[0] = Blocks<3>::bx + 4; box[1] = Blocks<3>::by + 4; box[2] = Blocks<3>::bz + 4; box[3] = 2;
+  cuuint32_t rank = 0;
+  CUtensorMapDataType type;
+  if (elem_bytes == 4) {
+    type = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    for (int a = 0; a < D; ++a) { dims[rank] = ext[a]; box[rank] = tile[a]; ++rank; }
   } else {
-    rank = 3;
-    dims[0] = d.px; dims[1] = d.py; dims[2] = 2;
-    strides[0] = (cuuint64_t)d.px * elem_bytes;
-    strides[1] = (cuuint64_t)d.PN * elem_bytes;
-    box[0] = Blocks<2>::bx + 4; box[1] = Blocks<2>::by + 4; box[2] = 2;
+    type = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    dims[0] = 2; box[0] = 2; rank = 1;
+    for (int a = 0; a < D; ++a) { dims[rank] = ext[a]; box[rank] = tile[a]; ++rank; }
+  }
+  // byte strides of dimensions 1..rank-1
+  cuuint64_t stride = elem_bytes == 4 ? pair_bytes : elem_bytes;
+  for (cuuint32_t k = 1; k < rank; ++k) {
+    stride *= dims[k - 1];
+    strides[k - 1] = stride;
   }
   const CUresult r = encode(map, type, rank, d.aux, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -93,6 +109,47 @@ inline bool make_aux_map(CUtensorMap* map, const DevDomain& d, int D, size_t ele
     return false;
   }
   return true;
+}
+
+// Tensor map over the q_a planes (element offset 2 PN of d.aux, one plane per
+// axis): a (px, py[, pz], D) tensor with a box of (Blocks::bx + 4, Blocks::by + 2
+// [, Blocks::bz + 2], 1), which holds q_a at the tile's nodes and their +-1
+// neighbours along every axis (x starts 2 nodes early so that the box starts on a
+// 16-byte boundary).
+inline bool make_q_map(CUtensorMap* map, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
+  const tensor_map_encode_fn encode = tensor_map_encoder(why);
+  if (!encode) return false;
+  const cuuint64_t e = elem_bytes;
+  cuuint64_t dims[4], strides[3];
+  cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+  const cuuint32_t rank = (cuuint32_t)D + 1;
+  dims[0] = d.px; dims[1] = d.py;
+  strides[0] = d.px * e;
+  box[0] = (D == 3 ? Blocks<3>::bx : Blocks<2>::bx) + 4;
+  box[1] = (D == 3 ? Blocks<3>::by : Blocks<2>::by) + 2;
+  if (D == 3) {
+    dims[2] = d.pz; dims[3] = 3;
+    strides[1] = (cuuint64_t)d.px * d.py * e;
+    strides[2] = (cuuint64_t)d.PN * e;
+    box[2] = Blocks<3>::bz + 2; box[3] = 1;
+  } else {
+    dims[2] = 2;
+    strides[1] = (cuuint64_t)d.PN * e;
+    box[2] = 1;
+  }
+  void* base = (char*)d.aux + 2 * (size_t)d.PN * elem_bytes;
+  const CUresult r = encode(map, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                            rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *why = "cuTensorMapEncodeTiled rejected the q tensor map";
+    return false;
+  }
+  return true;
+}
+
+inline bool make_tile_maps(TileMaps* m, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
+  return make_aux_map(&m->aux, d, D, elem_bytes, why) && make_q_map(&m->q, d, D, elem_bytes, why);
 }
 
 // Final fixed-order reduction of the diagnostic partial sums (lbm_d2q9.cu).

@@ -19,8 +19,9 @@ def case(D, nx, ny, nz=1, *, Tr=0.8, kappa=0.002, nu_l=0.05, nu_v=0.15, walls=Fa
     else:
         rv, rl = rho_v, rho_l
     bc = [0] * 6
-    if walls:
-        ax = 1 if D == 2 else 2
+    # walls=True: bounce-back walls across the last axis; a tuple: across those axes
+    axes = ((1 if D == 2 else 2),) if walls is True else (tuple(walls) if walls else ())
+    for ax in axes:
         bc[2 * ax] = bc[2 * ax + 1] = 1
     return dict(D=D, nx=nx, ny=ny, nz=nz if D == 3 else 1, Tr=Tr, kappa=kappa, nu_l=nu_l, nu_v=nu_v,
                 rho_l=rl, rho_v=rv, bc=tuple(bc), g=tuple(g), gamma_mode=gamma_mode,

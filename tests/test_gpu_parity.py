@@ -30,6 +30,8 @@ CASES = {
     "d2q9_walls": dict(D=2, nx=67, ny=29, walls=True),
     "d3q27_periodic": dict(D=3, nx=37, ny=13, nz=11),
     "d3q27_walls": dict(D=3, nx=35, ny=9, nz=12, walls=True),
+    "d2q9_xwalls": dict(D=2, nx=66, ny=21, walls=(0,)),
+    "d3q27_allwalls": dict(D=3, nx=34, ny=10, nz=9, walls=(0, 1, 2)),
 }
 
 
@@ -59,10 +61,11 @@ def test_one_step_matches_oracle(name, precision):
 
 
 @pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_FP32], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("name", ["d2q9_walls", "d3q27_walls"])
+@pytest.mark.parametrize("name", list(CASES))
 def test_multi_step_trajectory_matches_oracle(name, precision):
-    """Three steps cover both A-A parities (even, odd, even) and the bounce-back
-    reads and writes of each; the error bound grows with the step count."""
+    """Three steps cover both A-A parities (even, odd, even): the odd step reads and
+    writes the neighbours' slots, across periodic wraps and bounce-back walls on
+    every axis; the error bound grows with the step count."""
     c = case(**CASES[name], precision=precision)
     f0 = as_storage(drop_state(c), precision)
     fg, fo = run_both(c, f0, 3)
