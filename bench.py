@@ -44,7 +44,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -60,7 +60,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -136,7 +136,8 @@ CPU_CROP = (48, 64, 64)   # nz, ny, nx: 196,608 nodes
 CPU_STEPS = 12
 
 
-def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
+def oracle_crop_state(wl, crop=CPU_CROP):
+    """Oracle parameters and initial populations of a crop of the workload."""
     import oracle as O
     from oracle import thermo
     from paper_2201_12404_gb300 import workloads as WL
@@ -149,7 +150,13 @@ def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
     p = O.make_params(wl.D, nx, ny, nz, T_over_Tc=wl.T_over_Tc, kappa=wl.kappa, nu_liquid=nu_l,
                       nu_vapour=nu_v, rho_liquid=rl, rho_vapour=rv, bc=bc, **WL.PAPER_EOS)
     rho, u = WL.initial_fields(wl, rv, rl, crop=crop)
-    f = O.init_physical(p, rho, u)
+    return p, O.init_physical(p, rho, u)
+
+
+def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
+    import oracle as O
+    p, f = oracle_crop_state(wl, crop)
+    nz, ny, nx = crop
     t0 = time.perf_counter()
     O.run(p, f, steps)
     dt = time.perf_counter() - t0
@@ -159,26 +166,44 @@ def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
                       f"workload (same EOS, kappa, viscosities, walls), {dt:.1f} s"}
 
 
+def metric_and_config(args, wl, world):
+    """Metric name and config of a benchmark line (shared by both arms)."""
+    pop_bytes = {"fp64": 8, "fp32": 4, "fp16dev": 2}[args.precision]
+    metric = f"D3Q27 entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)"
+    config = {"workload": wl.name, "nodes": wl.N, "lattice": "D3Q27", "storage": f"{args.precision} A-A",
+              "l2": f"inputs larger than L2 ({27 * pop_bytes * wl.N / 1e9:.2f} GB populations), no flush",
+              "parallelism": f"replicas{world}" if world > 1 else "single GPU"}
+    return metric, config
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores, one
+    oracle step of a bounded crop of the workload per benchmark step (rank 0 only)."""
+    import oracle as O
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     from paper_2201_12404_gb300 import workloads as WL
     wl = WL.by_name(args.workload)
+    p, f = oracle_crop_state(wl, CPU_CROP)
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up effects worth a full sample; the first timed sample includes none
-    vals = []
+        f, _g = O.run(p, f, 1)
+    times = []
     for _ in range(max(1, args.steps)):
-        vals.append(oracle_sample(wl, steps=1, crop=CPU_CROP))
-    v = float(np.median([x["value"] for x in vals]))
-    cb = dict(vals[0])
-    cb["value"] = v
-    cb["sample"] = (f"FP64 oracle, 1 step of a {CPU_CROP[2]}x{CPU_CROP[1]}x{CPU_CROP[0]} crop per benchmark "
-                    f"step (median of {len(vals)})")
-    line = {"impl": "reference", "metric": "D3Q27 entropic-MRT MLUPS", "value": v, "unit": "MLUPS",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic", "config": {"workload": wl.name, "oracle_crop": list(CPU_CROP)},
-            "cpu_baseline": cb,
+        t0 = time.perf_counter()
+        f, _g = O.run(p, f, 1)
+        times.append(time.perf_counter() - t0)
+    nodes = CPU_CROP[0] * CPU_CROP[1] * CPU_CROP[2]
+    v = nodes * len(times) / sum(times) / 1e6
+    metric, config = metric_and_config(args, wl, world)
+    config["oracle_crop"] = f"{CPU_CROP[2]}x{CPU_CROP[1]}x{CPU_CROP[0]}"
+    sample = (f"FP64 oracle, {len(times)} steps of a {CPU_CROP[2]}x{CPU_CROP[1]}x{CPU_CROP[0]} crop of the same "
+              f"D3Q27 drop-on-film workload, one per benchmark step, {sum(times):.1f} s")
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -285,15 +310,14 @@ def run_ours(args):
     achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
     traffic = recorded_traffic("d3q27_fp32_collide_stream") if (args.precision == "fp32" and wl.N == 512 * 512 * 256) else None
     Q = 27
+    metric, config = metric_and_config(args, wl, world)
     line = {
-        "metric": f"D3Q27 entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)",
+        "metric": metric,
         "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16dev": "f16 storage, f32 arithmetic"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": wl.name, "nodes": wl.N, "lattice": "D3Q27", "storage": f"{args.precision} A-A",
-                   "l2": f"inputs larger than L2 ({27 * pop_bytes * wl.N / 1e9:.2f} GB populations), no flush",
-                   "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
+        "config": config,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "collide_stream (force + collide + stream)",
@@ -318,7 +342,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

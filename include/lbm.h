@@ -171,6 +171,15 @@ size_t lbm_footprint_bytes(const lbm_params* p);
  * liquid and the saturation pressure.  Host-only. */
 lbm_status lbm_coexistence(const lbm_params* p, double* rho_vapour, double* rho_liquid, double* p_sat);
 
+/* Densities on (0, 1/b) where P(rho) - rho cs^2 changes sign for the EOS fields
+ * of p: the sign s of the pseudo-potential (Sec. 2.3; s = +1 where P > rho cs^2,
+ * -1 otherwise, including equality) flips there.  Writes them ascending into
+ * changes[0..n-1] (n <= 3, the rest +inf), each the first float64 density with
+ * the new sign, and the sign below changes[0] into *s0; the kernels decide s
+ * this way.  Host-only; LBM_ERR_INVALID_ARG for NULL pointers or a, b, R,
+ * T/Tc not positive. */
+lbm_status lbm_psi_sign_changes(const lbm_params* p, double changes[3], int* n, double* s0);
+
 /* Kernel timing on the domain's stream with CUDA events.  When enabled, every
  * launch made by lbm_step is bracketed by events; lbm_kernel_times then
  * synchronises and returns, per kernel kind, the summed milliseconds and the

@@ -247,6 +247,18 @@ size_t lbm_footprint_bytes(const lbm_params* p) {
   return s.f_bytes + s.aux_bytes + s.rho_w_bytes + sizeof(unsigned int) + sizeof(unsigned long long);
 }
 
+lbm_status lbm_psi_sign_changes(const lbm_params* p, double changes[3], int* n, double* s0) {
+  if (!p || !changes || !n || !s0) { g_create_error = "NULL argument"; return LBM_ERR_INVALID_ARG; }
+  if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0) || !(p->T_over_Tc > 0)) {
+    g_create_error = "the sign changes need a, b, R, T/Tc > 0";
+    return LBM_ERR_INVALID_ARG;
+  }
+  lbm::psi_sign_changes(eos_coeffs(*p), changes, s0);
+  *n = 0;
+  for (int k = 0; k < 3; ++k) *n += std::isfinite(changes[k]) ? 1 : 0;
+  return LBM_OK;
+}
+
 lbm_status lbm_coexistence(const lbm_params* p, double* rho_vapour, double* rho_liquid, double* p_sat) {
   if (!p || !rho_vapour || !rho_liquid) { g_create_error = "NULL argument"; return LBM_ERR_INVALID_ARG; }
   if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0) || !(p->T_over_Tc > 0) || !(p->T_over_Tc < 1)) {

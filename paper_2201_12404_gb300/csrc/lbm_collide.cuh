@@ -553,7 +553,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   }
 
   // ---- stream: A-A write
-  const XBase xb = xbase(d, x, n);
+  const XBase xb = xbase<S>(d, x, n);
   auto store = [&](bool in) {
 #pragma unroll
     for (int ix = 0; ix < 3; ++ix) {
@@ -594,7 +594,7 @@ __device__ __forceinline__ void stage_populations(const DevDomain& d, int x, int
   constexpr int Q = Lattice<D>::Q;
   if (!(x < d.nx && y < d.ny && z < d.nz)) return;
   const long long n = node_of(d, x, y, z);
-  const XBase xb = xbase(d, x, n);
+  const XBase xb = xbase<S>(d, x, n);
   if (P == 0 || fast_links<D>(d, x, y, z)) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) cp_async_word<sizeof(S)>(s_f + i * NT + tid, src_ptr<D, P, S>(d, true, xb, x, y, z, n, i));

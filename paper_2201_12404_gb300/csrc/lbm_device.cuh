@@ -153,13 +153,20 @@ __device__ __forceinline__ bool fast_links(const DevDomain& d, int x, int y, int
 }
 
 // Node index n of (x, y, z) corrected for the periodic x wrap of the neighbour
-// r - c along x: b[c + 1], c = -1, 0, +1 (used by fast_links nodes only).
-struct XBase { long long b[3]; };
+// r - c along x: b[c + 1], c = -1, 0, +1 (used by fast_links nodes only), and the
+// byte address of slot 0 of each in the population array (elements of S).
+struct XBase {
+  long long b[3];
+  char* p[3];
+};
+template <typename S>
 __device__ __forceinline__ XBase xbase(const DevDomain& d, int x, long long n) {
   XBase r;
   r.b[0] = x == d.nx - 1 ? n - d.nx : n;  // x + 1 wraps to 0
   r.b[1] = n;
   r.b[2] = x == 0 ? n + d.nx : n;         // x - 1 wraps to nx - 1
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.p[k] = (char*)((S*)d.f + r.b[k]);
   return r;
 }
 
@@ -180,8 +187,8 @@ __device__ __forceinline__ S* src_ptr(const DevDomain& d, bool fast, const XBase
                                       int i) {
   constexpr int Q = Lattice<D>::Q;
   S* F = (S*)d.f;
-  if (P == 0) return (S*)((char*)(F + n) + d.src_boff[0][i]);
-  if (fast) return (S*)((char*)(F + xb.b[cxi(i) + 1]) + d.src_boff[1][i]);
+  if (P == 0) return (S*)(xb.p[1] + d.src_boff[0][i]);
+  if (fast) return (S*)(xb.p[cxi(i) + 1] + d.src_boff[1][i]);
   bool wall = false;
   const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
@@ -197,8 +204,8 @@ __device__ __forceinline__ S* dst_ptr(const DevDomain& d, bool fast, const XBase
                                       int i) {
   constexpr int Q = Lattice<D>::Q;
   S* F = (S*)d.f;
-  if (P == 0) return (S*)((char*)(F + n) + d.dst_boff[0][i]);
-  if (fast) return (S*)((char*)(F + xb.b[1 - cxi(i)]) + d.dst_boff[1][i]);
+  if (P == 0) return (S*)(xb.p[1] + d.dst_boff[0][i]);
+  if (fast) return (S*)(xb.p[1 - cxi(i)] + d.dst_boff[1][i]);
   bool wall = false;
   const int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
@@ -223,7 +230,7 @@ template <int D, int P, typename S, typename R>
 __device__ __forceinline__ void gather(const DevDomain& d, int x, int y, int z, R* f) {
   constexpr int Q = Lattice<D>::Q;
   const long long n = node_of(d, x, y, z);
-  const XBase xb = xbase(d, x, n);
+  const XBase xb = xbase<S>(d, x, n);
   if constexpr (DevStorage<S>::value) {
     // f_i = w_i rho_w (1 + delta_i)
     const float* rw = d.rho_w[P];

@@ -89,7 +89,7 @@ __global__ void init_equilibrium_kernel(DevDomain d, const double* rho, const do
     // next step (even parity) decodes with rho_w[0] of that node
     const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
     const bool fast = fast_links<D>(d, x, y, z);
-    const XBase xb = xbase(d, x, n);
+    const XBase xb = xbase<S>(d, x, n);
     d.rho_w[0][n] = (float)r;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -128,7 +128,7 @@ __global__ void canonical_write_kernel(DevDomain d, const double* in) {
     // rho_w[0] holds every node's density (canonical_density_kernel, launched before)
     const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
     const bool fast = fast_links<D>(d, x, y, z);
-    const XBase xb = xbase(d, x, n);
+    const XBase xb = xbase<S>(d, x, n);
     for (int i = 0; i < Q; ++i) {
       const double rw = (double)d.rho_w[0][upstream_node<D>(d, fast, xb, x, y, z, n, i)];
       F[(long long)i * d.N + n] = __float2half_rn((float)(in[(long long)i * d.N + n] / (wq<D>(i) * rw) - 1.0));

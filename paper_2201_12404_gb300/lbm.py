@@ -87,6 +87,7 @@ def load():
                 "lbm_guard_count": (st, [H, ctypes.POINTER(ctypes.c_uint64)]),
                 "lbm_footprint_bytes": (ctypes.c_size_t, [P]),
                 "lbm_coexistence": (st, [P, _dp, _dp, _dp]),
+                "lbm_psi_sign_changes": (st, [P, _dp, ctypes.POINTER(ctypes.c_int), _dp]),
                 "lbm_set_timing": (st, [H, ctypes.c_int]),
                 "lbm_kernel_times": (st, [H, _dp, ctypes.POINTER(ctypes.c_int64)]),
                 "lbm_launch_count": (ctypes.c_int64, [H]),
@@ -140,6 +141,14 @@ def lbm_coexistence(p: lbm_params):
     rv, rl, ps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().lbm_coexistence(ctypes.byref(p), ctypes.byref(rv), ctypes.byref(rl), ctypes.byref(ps)))
     return rv.value, rl.value, ps.value
+
+
+def lbm_psi_sign_changes(p: lbm_params):
+    """(densities where P - rho cs^2 changes sign, ascending; sign below the first)."""
+    ch = (ctypes.c_double * 3)()
+    n, s0 = ctypes.c_int(), ctypes.c_double()
+    _check(load().lbm_psi_sign_changes(ctypes.byref(p), ch, ctypes.byref(n), ctypes.byref(s0)))
+    return [ch[k] for k in range(n.value)], s0.value
 
 
 def lbm_version() -> str:

@@ -13,7 +13,7 @@ PAPER_EOS = dict(a=0.003, b=0.095, R=1.0, acentric=0.344)
 
 
 def case(D, nx, ny, nz=1, *, Tr=0.8, kappa=0.002, nu_l=0.05, nu_v=0.15, walls=False, g=(0.0, 0.0, 0.0),
-         gamma_mode=0, gamma_value=2.0, precision=lbm.LBM_FP64, eos_fp64=1, rho_l=None, rho_v=None):
+         gamma_mode=0, gamma_value=2.0, precision=lbm.LBM_FP64, eos_fp64=1, rho_l=None, rho_v=None, a=None):
     if rho_l is None:
         rv, rl, _ = thermo.maxwell(Tr, **PAPER_EOS)
     else:
@@ -25,14 +25,15 @@ def case(D, nx, ny, nz=1, *, Tr=0.8, kappa=0.002, nu_l=0.05, nu_v=0.15, walls=Fa
         bc[2 * ax] = bc[2 * ax + 1] = 1
     return dict(D=D, nx=nx, ny=ny, nz=nz if D == 3 else 1, Tr=Tr, kappa=kappa, nu_l=nu_l, nu_v=nu_v,
                 rho_l=rl, rho_v=rv, bc=tuple(bc), g=tuple(g), gamma_mode=gamma_mode,
-                gamma_value=gamma_value, precision=precision, eos_fp64=eos_fp64)
+                gamma_value=gamma_value, precision=precision, eos_fp64=eos_fp64,
+                eos=dict(PAPER_EOS, **({} if a is None else {"a": a})))
 
 
 def oracle_params(c):
     return O.make_params(c["D"], c["nx"], c["ny"], c["nz"], T_over_Tc=c["Tr"], kappa=c["kappa"],
                          nu_liquid=c["nu_l"], nu_vapour=c["nu_v"], rho_liquid=c["rho_l"],
                          rho_vapour=c["rho_v"], g=c["g"], bc=c["bc"], gamma_mode=c["gamma_mode"],
-                         gamma_value=c["gamma_value"], **PAPER_EOS)
+                         gamma_value=c["gamma_value"], **c.get("eos", PAPER_EOS))
 
 
 def lbm_params(c):
@@ -41,7 +42,7 @@ def lbm_params(c):
         nx=c["nx"], ny=c["ny"], nz=c["nz"], T_over_Tc=c["Tr"], kappa=c["kappa"],
         nu_liquid=c["nu_l"], nu_vapour=c["nu_v"], rho_liquid=c["rho_l"], rho_vapour=c["rho_v"],
         body_force=c["g"], bc=c["bc"], gamma_mode=c["gamma_mode"], gamma_value=c["gamma_value"],
-        eos_fp64=c["eos_fp64"], **PAPER_EOS)
+        eos_fp64=c["eos_fp64"], **c.get("eos", PAPER_EOS))
 
 
 def shape(c):

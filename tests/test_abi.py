@@ -116,3 +116,31 @@ def test_library_maxwell_matches_oracle(L, Tr):
 
 def test_version_string(L):
     assert "sm_103a" in lbm.lbm_version()
+
+
+@pytest.mark.parametrize("Tr,a", [(0.59, 0.003), (0.8, 0.003), (0.95, 0.003), (1.2, 0.003), (0.7, 2.0 / 49.0), (3.0, 0.003),
+                                  (0.6, 0.5), (0.9, 0.5)])
+def test_psi_sign_changes_match_oracle_sign(L, Tr, a):
+    """The densities where the library flips s (Sec. 2.3) reproduce the oracle's
+    pointwise sign of P - rho cs^2 on a dense sample of (0, 1/b), and the sign
+    flips across each of them."""
+    import numpy as np
+    import oracle as O
+    from cases import case, oracle_params
+    p = lbm.lbm_default_params(T_over_Tc=Tr, a=a)
+    changes, s0 = lbm.lbm_psi_sign_changes(p)
+    assert len(changes) <= 3 and changes == sorted(changes) and s0 in (-1.0, 1.0)
+    op = oracle_params(case(2, 8, 8, Tr=Tr, rho_l=2.0, rho_v=1.0))
+    op.a = a
+    top = 1.0 / p.b
+    grid = np.concatenate([top * np.logspace(-12, -3, 400), np.linspace(top * 1e-3, top * (1 - 1e-9), 6000)])
+
+    def lib_sign(r):
+        return s0 * (-1.0) ** sum(1 for t in changes if r >= t)
+
+    mismatches = [r for r in grid if lib_sign(r) != O.psi(op, float(r))[1]]
+    assert not mismatches, mismatches[:5]
+    for t in changes:
+        below, above = t * (1 - 1e-12), t * (1 + 1e-12)
+        assert O.psi(op, below)[1] == lib_sign(below) and O.psi(op, above)[1] == lib_sign(above)
+        assert lib_sign(below) == -lib_sign(above)

@@ -52,3 +52,20 @@ def test_reference_arm_only_rank0_works(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_gpu_arm_helpers_resolve_and_count_bytes():
+    """The helpers the GPU arm calls exist and give the per-launch byte counts
+    the roofline line reports (236 B per node for FP32 D3Q27)."""
+    from paper_2201_12404_gb300 import workloads as WL
+    wl = WL.by_name("drop3d")
+    assert bench.algorithmic_bytes_k2(wl, 4, 4) == 236 * wl.N
+    assert bench.algorithmic_bytes_k2(wl, 8, 8) == 472 * wl.N
+    t = bench.recorded_traffic("d3q27_fp32_collide_stream")
+    assert t is None or 0.8 * 236 * wl.N < t < 1.5 * 236 * wl.N
+    assert bench.recorded_traffic("no such kernel") is None
+
+    class Args:
+        precision = "fp32"
+    metric, config = bench.metric_and_config(Args(), wl, 1)
+    assert "D3Q27" in metric and config["nodes"] == wl.N

@@ -92,6 +92,19 @@ def test_body_force_and_upper_pressure_branch_match_oracle():
     assert rel_err(fg, fo, 2).max() <= 2e-12
 
 
+@pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_FP32], ids=["fp64", "fp32"])
+def test_two_sign_changes_of_p_minus_p0_match_oracle(precision):
+    """An EOS (a = 0.5, T/Tc = 0.6) with P - rho cs^2 changing sign at two densities
+    (0.33 and 8.9): the drop's densities 0.2 .. 1.0 straddle the lower one, so s
+    takes both values in the force stencils, across both A-A parities."""
+    c = case(2, 40, 26, Tr=0.6, a=0.5, rho_l=1.0, rho_v=0.2, kappa=0.001, precision=precision)
+    changes, _ = lbm.lbm_psi_sign_changes(lbm_params(c))
+    assert len(changes) == 2 and 0.2 < changes[0] < 1.0
+    f0 = as_storage(drop_state(c, perturb=0.002), precision)
+    fg, fo = run_both(c, f0, 3)
+    assert rel_err(fg, fo, 2).max() <= 4 * TOL[precision]
+
+
 @pytest.mark.parametrize("eos_fp64", [0, 2])
 def test_fp32_eos_modes_match_oracle(eos_fp64):
     c = case(3, 24, 10, 9, precision=lbm.LBM_FP32, eos_fp64=eos_fp64)
