@@ -16,6 +16,7 @@ oracle on a bounded crop of the same workload on the host cores.
 
 --impl reference times the FP64 CPU oracle (the reference implementation of
 the method) on a bounded crop of the same workload; N > 1: rank 0 only.
+--workload drop2d runs the D2Q9 drop impact (2048x1024) the same way.
 """
 from __future__ import annotations
 
@@ -133,6 +134,7 @@ def barrier(world):
 # CPU oracle on a bounded crop of the workload
 # ---------------------------------------------------------------------------
 CPU_CROP = (48, 64, 64)   # nz, ny, nx: 196,608 nodes
+CPU_CROP_2D = (1, 384, 512)
 CPU_STEPS = 12
 
 
@@ -153,8 +155,17 @@ def oracle_crop_state(wl, crop=CPU_CROP):
     return p, O.init_physical(p, rho, u)
 
 
-def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
+def crop_of(wl):
+    return CPU_CROP if wl.D == 3 else CPU_CROP_2D
+
+
+def lattice_of(wl):
+    return "D3Q27" if wl.D == 3 else "D2Q9"
+
+
+def oracle_sample(wl, steps=CPU_STEPS, crop=None):
     import oracle as O
+    crop = crop or crop_of(wl)
     p, f = oracle_crop_state(wl, crop)
     nz, ny, nx = crop
     t0 = time.perf_counter()
@@ -162,16 +173,36 @@ def oracle_sample(wl, steps=CPU_STEPS, crop=CPU_CROP):
     dt = time.perf_counter() - t0
     lups = nx * ny * nz * steps
     return {"value": lups / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle, {steps} steps of a {nx}x{ny}x{nz} crop of the same D3Q27 drop-on-film "
+            "sample": f"FP64 oracle, {steps} steps of a {nx}x{ny}x{nz} crop of the same {lattice_of(wl)} drop-on-film "
                       f"workload (same EOS, kappa, viscosities, walls), {dt:.1f} s"}
+
+
+L2_BYTES = 129e6  # GB300 L2 (the device query below replaces it when available)
+
+
+def l2_note(pop_bytes_total):
+    """How the timed steps stand against L2: the populations of the default
+    workload are far larger than L2, so consecutive steps cannot hit in it."""
+    l2 = L2_BYTES
+    try:
+        import torch
+        if torch.cuda.is_available():
+            l2 = float(getattr(torch.cuda.get_device_properties(0), "L2_cache_size", l2) or l2)
+    except Exception:
+        pass
+    if pop_bytes_total > 4 * l2:
+        return f"inputs larger than L2 ({pop_bytes_total / 1e9:.2f} GB populations vs {l2 / 1e6:.0f} MB L2), no flush"
+    return (f"populations ({pop_bytes_total / 1e6:.0f} MB) within a few times the {l2 / 1e6:.0f} MB L2: "
+            f"L2-resident throughput, no flush")
 
 
 def metric_and_config(args, wl, world):
     """Metric name and config of a benchmark line (shared by both arms)."""
     pop_bytes = {"fp64": 8, "fp32": 4, "fp16dev": 2}[args.precision]
-    metric = f"D3Q27 entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)"
-    config = {"workload": wl.name, "nodes": wl.N, "lattice": "D3Q27", "storage": f"{args.precision} A-A",
-              "l2": f"inputs larger than L2 ({27 * pop_bytes * wl.N / 1e9:.2f} GB populations), no flush",
+    Q = 27 if wl.D == 3 else 9
+    metric = f"{lattice_of(wl)} entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)"
+    config = {"workload": wl.name, "nodes": wl.N, "lattice": lattice_of(wl), "storage": f"{args.precision} A-A",
+              "l2": l2_note(Q * pop_bytes * wl.N),
               "parallelism": f"replicas{world}" if world > 1 else "single GPU"}
     return metric, config
 
@@ -185,7 +216,8 @@ def run_reference(args):
         return 0
     from paper_2201_12404_gb300 import workloads as WL
     wl = WL.by_name(args.workload)
-    p, f = oracle_crop_state(wl, CPU_CROP)
+    crop = crop_of(wl)
+    p, f = oracle_crop_state(wl, crop)
     for _ in range(args.warmup):
         f, _g = O.run(p, f, 1)
     times = []
@@ -193,12 +225,12 @@ def run_reference(args):
         t0 = time.perf_counter()
         f, _g = O.run(p, f, 1)
         times.append(time.perf_counter() - t0)
-    nodes = CPU_CROP[0] * CPU_CROP[1] * CPU_CROP[2]
+    nodes = crop[0] * crop[1] * crop[2]
     v = nodes * len(times) / sum(times) / 1e6
     metric, config = metric_and_config(args, wl, world)
-    config["oracle_crop"] = f"{CPU_CROP[2]}x{CPU_CROP[1]}x{CPU_CROP[0]}"
-    sample = (f"FP64 oracle, {len(times)} steps of a {CPU_CROP[2]}x{CPU_CROP[1]}x{CPU_CROP[0]} crop of the same "
-              f"D3Q27 drop-on-film workload, one per benchmark step, {sum(times):.1f} s")
+    config["oracle_crop"] = f"{crop[2]}x{crop[1]}x{crop[0]}"
+    sample = (f"FP64 oracle, {len(times)} steps of a {crop[2]}x{crop[1]}x{crop[0]} crop of the same "
+              f"{lattice_of(wl)} drop-on-film workload, one per benchmark step, {sum(times):.1f} s")
     line = {"impl": "reference", "metric": metric, "value": v, "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
@@ -309,7 +341,7 @@ def run_ours(args):
         k2_bytes += wl.N * 8  # writer densities: one read (the neighbours' are cache hits), one write
     achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
     traffic = recorded_traffic("d3q27_fp32_collide_stream") if (args.precision == "fp32" and wl.N == 512 * 512 * 256) else None
-    Q = 27
+    Q = 27 if wl.D == 3 else 9
     metric, config = metric_and_config(args, wl, world)
     line = {
         "metric": metric,
@@ -348,8 +380,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16dev"], default="fp32",
                     help="population storage/arithmetic of the timed path (fp32 is the headline)")
-    ap.add_argument("--workload", default="drop3d", help="drop3d (default, 512x512x256) or drop3d-small "
-                    "(256x256x128, the profiling case)")
+    ap.add_argument("--workload", default="drop3d", choices=["drop3d", "drop3d-small", "drop2d"],
+                    help="drop3d (default, D3Q27 512x512x256), drop3d-small (256x256x128, the profiling "
+                    "case) or drop2d (D2Q9 2048x1024)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
