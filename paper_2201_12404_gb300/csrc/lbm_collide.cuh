@@ -142,15 +142,15 @@ __device__ __forceinline__ R entropic_gamma(R sA, R sB, R om) {
   const float A = (float)sA, B = (float)sB;
   double ratio = 0.0;
   if (B > 1e-37f) {
-    // float quotient refined once in float64: r = q + (A - q B)/B, the residual
-    // A - q B being exact in a float64 fma of float operands
+    // the float32 quotient q and its correction e = (A - q B)/B, the residual being
+    // exact in one float32 fma, summed in float64
     const float q = A / B;
-    const double r0 = (double)q;
-    const double res = fma(-r0, (double)B, (double)A);
-    ratio = r0 + res * (double)__frcp_rn(B);
+    const float e = fmaf(-q, B, A) * __frcp_rn(B);
+    ratio = (double)q + (double)e;
   }
-  const double tw = 2.0 * (double)__frcp_rn((float)om);
-  return (R)(tw - (2.0 - tw) * ratio);
+  // gamma/2 = 1/omega + (1/omega - 1) ratio
+  const float iom = __frcp_rn((float)om);
+  return (R)(2.0f * (float)fma((double)(iom - 1.0f), ratio, (double)iom));
 }
 
 // Dynamic shared memory of the persistent kernel: h_i and the staged
@@ -329,30 +329,45 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   //      and (4/3) psi(r+c) - (1/6) psi(r+2c) is (2, 4/3) times v(r+c) + (-1/2, -1/8) v(r+2c),
   //      the common (2, 4/3) applied once at the end.
   const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
-  const R2 cb = two<R>((R)-0.5, (R)-0.125);
-  R2 GX = zero2, GY = zero2, GZ = zero2;
+  //      Rows are summed by weight class (w_y w_z: centre 2 (2/3), edge 1/2 (2/3) or
+  //      2 (1/6), corner 1/2 (1/6); 2-D: 2, 1/2) and the weights applied once: GX =
+  //      (1/6) sum w_yz (t(+1) - t(-1)), and the y/z components use u = t(-1) + t(+1) +
+  //      4 t(0) = 6 x (the row's weighted sum over cx).
+  const R2 cb = two<R>((R)-0.5, (R)-0.125), four = both<R>((R)4);
+  R2 DXc = zero2, DXe = zero2, DXk = zero2, YE = zero2, YK = zero2, ZE = zero2, ZK = zero2;
 #pragma unroll
   for (int row = 0; row < Q / 3; ++row) {
     const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
-    const R wyz = (cy == 0 ? (R)2 : (R)0.5) * (D == 3 ? (cz == 0 ? (R)(2.0 / 3.0) : (R)(1.0 / 6.0)) : (R)1);
     const int orow = HX * (cy + HY * cz);
     const Two<A>* p1 = s_aux + sc + orow;
     const Two<A>* p2 = s_aux + sc + 2 * orow;
     auto v = [](const Two<A>& a) { return two<R>((R)a.x, (R)a.y); };
-    // row terms at cx = -1 and +1 (x weights 1/6, signs -1, +1) and cx = 0 (weight 2/3)
     const R2 tm = fma2(cb, v(p2[-2]), v(p1[-1]));
     const R2 tp = fma2(cb, v(p2[2]), v(p1[1]));
-    GX = fma2(both<R>(wyz * (R)(1.0 / 6.0)), sub2(tp, tm), GX);
-    R2 srow;
-    if (row == (Q / 3) / 2) {
-      srow = mul2(both<R>(wyz * (R)(1.0 / 6.0)), add2(tp, tm));
-    } else {
-      const R2 t0 = fma2(cb, v(p2[0]), v(p1[0]));
-      srow = fma2(both<R>(wyz * (R)(1.0 / 6.0)), add2(tp, tm), mul2(both<R>(wyz * (R)(2.0 / 3.0)), t0));
+    const R2 dx = sub2(tp, tm);
+    if (cy == 0 && cz == 0) {
+      DXc = add2(DXc, dx);  // the centre row adds nothing to the y and z components
+      continue;
     }
-    if (cy != 0) GY = cy > 0 ? add2(GY, srow) : sub2(GY, srow);
-    if (D == 3 && cz != 0) GZ = cz > 0 ? add2(GZ, srow) : sub2(GZ, srow);
+    if (cy != 0 && cz != 0) DXk = add2(DXk, dx);
+    else DXe = add2(DXe, dx);
+    const R2 u = fma2(four, fma2(cb, v(p2[0]), v(p1[0])), add2(tp, tm));
+    if (cy != 0) {
+      R2& acc = cz == 0 ? YE : YK;
+      acc = cy > 0 ? add2(acc, u) : sub2(acc, u);
+    }
+    if (D == 3 && cz != 0) {
+      R2& acc = cy == 0 ? ZE : ZK;
+      acc = cz > 0 ? add2(acc, u) : sub2(acc, u);
+    }
   }
+  // class weights w_yz / 6 (3-D: 4/3, 1/3, 1/12; 2-D: 2, 1/2)
+  constexpr R wc = D == 3 ? (R)(4.0 / 18.0) : (R)(2.0 / 6.0);
+  constexpr R we = D == 3 ? (R)(1.0 / 18.0) : (R)(0.5 / 6.0);
+  constexpr R wk = (R)(1.0 / 72.0);
+  const R2 GX = fma2(both<R>(wc), DXc, fma2(both<R>(we), DXe, mul2(both<R>(wk), DXk)));
+  const R2 GY = fma2(both<R>(we), YE, mul2(both<R>(wk), YK));
+  const R2 GZ = fma2(both<R>(we), ZE, mul2(both<R>(wk), ZK));
   // s psi at the node: psi from the tile, s from the node's density in the tile
   const Two<A> c_aux = s_aux[sc];
   const R spsi_c = psi_sign<R>(ph, (R)c_aux.x) * (R)c_aux.y;
