@@ -154,6 +154,13 @@ lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count)
 lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* max_u,
                          double* gamma_field);
 
+/* Largest speed over the domain of the reported velocity u + F dt/(2 rho)
+ * (the exact-difference-method velocity that lbm_read_macroscopic returns,
+ * the velocity whose maximum the paper reports as the spurious current,
+ * Sec. 3.1.2), reduced on the GPU: one pass-1 launch for the current state,
+ * one reduction.  A state with a non-finite speed gives +inf.  Synchronising. */
+lbm_status lbm_max_speed(lbm_handle h, double* max_u);
+
 /* Turn per-node gamma recording on (enable != 0) or off for later lbm_step
  * calls.  Recording adds a float32 store per node and step (the 2/(omega gamma)
  * field of Sec. 3.3 is derived from it). */

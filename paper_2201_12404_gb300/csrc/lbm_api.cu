@@ -522,6 +522,26 @@ lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* 
   return LBM_OK;
 }
 
+lbm_status lbm_max_speed(lbm_handle h, double* max_u) {
+  LBM_LIVE(h);
+  if (!max_u) return fail(h, LBM_ERR_INVALID_ARG, "max_u is NULL");
+  lbm_status st = refresh_aux(h);
+  if (st != LBM_OK) return st;
+  const long long nblk = (h->dev.N + 255) / 256;
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)(nblk * 5 + 5) * sizeof(double), h->stream));
+  int nb = h->ops->max_speed_partial(h->dev, h->parity, buf, h->stream);
+  lbm::launch_diag_final(buf, nb, buf + nblk * 5, h->stream);
+  h->launches += 2;
+  LBM_CUDA(h, cudaGetLastError());
+  double out[5];
+  LBM_CUDA(h, cudaMemcpyAsync(out, buf + nblk * 5, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  *max_u = out[4];
+  return LBM_OK;
+}
+
 lbm_status lbm_record_gamma(lbm_handle h, int enable) {
   LBM_LIVE(h);
   h->record_gamma = enable != 0;

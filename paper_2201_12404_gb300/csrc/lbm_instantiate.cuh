@@ -90,9 +90,14 @@ struct Launch {
     diag_partial_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, partial);
     return (int)blocks1d(d);
   }
+  static int max_speed_partial(const DevDomain& d, int parity, double* partial, cudaStream_t s) {
+    max_speed_partial_kernel<D, S, R, A><<<blocks1d(d), 256, 0, s>>>(d, parity, partial);
+    return (int)blocks1d(d);
+  }
   static Ops table() {
     return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
-               &canonical_read, &canonical_write, &macroscopic, &bare_velocity, &diag_partial};
+               &canonical_read, &canonical_write, &macroscopic, &bare_velocity, &diag_partial,
+               &max_speed_partial};
   }
 };
 

@@ -150,6 +150,35 @@ __global__ void canonical_density_kernel(DevDomain d, const double* in) {
 }
 
 // ---------------------------------------------------------------------------
+// Force density F at node (x, y, z) from the auxiliary fields of the current
+// state (Eq. Kforce_final with the sign of reading R1), rho the node's density:
+// the link-by-link form of the stencil pass 2 evaluates row by row.
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename A>
+__device__ __forceinline__ void aux_force(const DevDomain& d, int x, int y, int z, R rho, R* F) {
+  constexpr int Q = Lattice<D>::Q;
+  const Two<A>* a2 = (const Two<A>*)d.aux;  // (rho, psi)
+  const long long pc = pnode_of<D>(d, x, y, z);
+  const long long sy = d.px, sz = (long long)d.px * d.py;
+  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
+  for (int i = 0; i < Q; ++i) {
+    if (i == Lattice<D>::REST) continue;
+    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
+    const R t4 = (R)(4.0 / 3.0) * (R)a2[pc + o].y - (R)(1.0 / 6.0) * (R)a2[pc + 2 * o].y;
+    const R t3 = (R)2 * (R)a2[pc + o].x - (R)a2[pc + 2 * o].x;
+    const R W = (R)(3.0 * wq<D>(i));
+    for (int a = 0; a < D; ++a) {
+      const int c = cq<D>(i, a);
+      g4[a] += W * (R)c * t4;
+      g3[a] += W * (R)c * t3;
+    }
+  }
+  const R spsi_c = psi_sign<R>(phys<R>(d), (R)a2[pc].x) * (R)a2[pc].y;
+  for (int a = 0; a < 3; ++a)
+    F[a] = a < D ? -((R)2 * spsi_c * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a] : (R)0;
+}
+
+// ---------------------------------------------------------------------------
 // Density and exact-difference-method velocity u + F/(2 rho); the auxiliary
 // fields must describe the current state (pass 1 run just before).
 // ---------------------------------------------------------------------------
@@ -163,27 +192,49 @@ __global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, dou
   gather<D, S, R>(d, parity, x, y, z, f);
   R rho, j[3], Pi[6];
   moments<D, R>(f, rho, j, Pi);
-  const Two<A>* a2 = (const Two<A>*)d.aux;  // (rho, psi)
-  const long long pc = pnode_of<D>(d, x, y, z);
-  const long long sy = d.px, sz = (long long)d.px * d.py;
-  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
-  for (int i = 0; i < Q; ++i) {
-    if (i == Lattice<D>::REST) continue;
-    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
-    const R t4 = (R)(4.0 / 3.0) * (R)a2[pc + o].y - (R)(1.0 / 6.0) * (R)a2[pc + 2 * o].y;
-    const R t3 = (R)2 * (R)a2[pc + o].x - (R)a2[pc + 2 * o].x;
-    const R W = (R)(3.0 * wq<D>(i));
-    for (int a = 0; a < D; ++a) {
-      const int c = cq<D>(i, a);
-      g4[a] += W * (R)c * t4;
-      g3[a] += W * (R)c * t3;
-    }
-  }
+  R F[3];
+  aux_force<D, R, A>(d, x, y, z, rho, F);
   rho_out[n] = (double)rho;
-  const R spsi_c = psi_sign<R>(phys<R>(d), (R)a2[pc].x) * (R)a2[pc].y;
-  for (int a = 0; a < D; ++a) {
-    const R Fa = -((R)2 * spsi_c * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
-    u_out[a * d.N + n] = (double)((j[a] + (R)0.5 * Fa) / rho);
+  for (int a = 0; a < D; ++a) u_out[a * d.N + n] = (double)((j[a] + (R)0.5 * F[a]) / rho);
+}
+
+// ---------------------------------------------------------------------------
+// Largest speed |u + F/(2 rho)| of the reported velocity (the velocity
+// macroscopic_kernel writes), one partial maximum per block in field 4 of the
+// [block][5] layout that diag_final_kernel reduces (fields 0-3 zero).  The
+// auxiliary fields must describe the current state.
+// ---------------------------------------------------------------------------
+template <int D, typename S, typename R, typename A>
+__global__ void __launch_bounds__(256) max_speed_partial_kernel(DevDomain d, int parity, double* partial) {
+  constexpr int Q = Lattice<D>::Q;
+  __shared__ double sh[256];
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double um = 0;
+  if (n < d.N) {
+    const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+    R f[Q];
+    gather<D, S, R>(d, parity, x, y, z, f);
+    R rho, j[3], Pi[6];
+    moments<D, R>(f, rho, j, Pi);
+    R F[3];
+    aux_force<D, R, A>(d, x, y, z, rho, F);
+    double u2 = 0;
+    for (int a = 0; a < D; ++a) {
+      const double ua = (double)((j[a] + (R)0.5 * F[a]) / rho);
+      u2 += ua * ua;
+    }
+    um = sqrt(u2);
+    if (!(um == um)) um = INFINITY;  // a non-finite state reports an infinite speed
+  }
+  sh[threadIdx.x] = um;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) partial[blockIdx.x * 5 + k] = 0.0;
+    partial[blockIdx.x * 5 + 4] = sh[0];
   }
 }
 
@@ -193,32 +244,13 @@ __global__ void macroscopic_kernel(DevDomain d, int parity, double* rho_out, dou
 // ---------------------------------------------------------------------------
 template <int D, typename R, typename A>
 __global__ void bare_velocity_kernel(DevDomain d, const double* rho_in, double* u) {
-  constexpr int Q = Lattice<D>::Q;
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.N) return;
   const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
-  const Two<A>* a2 = (const Two<A>*)d.aux;  // (rho, psi)
-  const long long pc = pnode_of<D>(d, x, y, z);
-  const long long sy = d.px, sz = (long long)d.px * d.py;
-  R g4[3] = {0, 0, 0}, g3[3] = {0, 0, 0};
-  for (int i = 0; i < Q; ++i) {
-    if (i == Lattice<D>::REST) continue;
-    const long long o = cxi(i) + sy * cyi(i) + (D == 3 ? sz * czi(i) : 0);
-    const R t4 = (R)(4.0 / 3.0) * (R)a2[pc + o].y - (R)(1.0 / 6.0) * (R)a2[pc + 2 * o].y;
-    const R t3 = (R)2 * (R)a2[pc + o].x - (R)a2[pc + 2 * o].x;
-    const R W = (R)(3.0 * wq<D>(i));
-    for (int a = 0; a < D; ++a) {
-      const int c = cq<D>(i, a);
-      g4[a] += W * (R)c * t4;
-      g3[a] += W * (R)c * t3;
-    }
-  }
-  const R rho = (R)a2[pc].x;
-  const R spsi_c = psi_sign<R>(phys<R>(d), rho) * (R)a2[pc].y;
-  for (int a = 0; a < D; ++a) {
-    const R Fa = -((R)2 * spsi_c * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a];
-    u[a * d.N + n] -= (double)Fa / (2.0 * rho_in[n]);
-  }
+  const R rho = (R)((const Two<A>*)d.aux)[pnode_of<D>(d, x, y, z)].x;
+  R F[3];
+  aux_force<D, R, A>(d, x, y, z, rho, F);
+  for (int a = 0; a < D; ++a) u[a * d.N + n] -= (double)F[a] / (2.0 * rho_in[n]);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,8 @@ struct Ops {
   void (*bare_velocity)(const DevDomain&, const double* rho, double* u, cudaStream_t);
   // returns the number of partial blocks written to partial (5 doubles each)
   int (*diag_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
+  // the same layout, field 4 = largest |u + F/(2 rho)| of the block (auxiliary fields current)
+  int (*max_speed_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
 };
 
 // Defined in lbm_d2q9.cu and lbm_d3q27.cu.

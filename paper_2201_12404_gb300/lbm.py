@@ -84,6 +84,7 @@ def load():
                 "lbm_write_populations": (st, [H, _dp, ctypes.c_size_t]),
                 "lbm_read_diag": (st, [H, _dp, _dp, _dp, _dp]),
                 "lbm_record_gamma": (st, [H, ctypes.c_int]),
+                "lbm_max_speed": (st, [H, _dp]),
                 "lbm_guard_count": (st, [H, ctypes.POINTER(ctypes.c_uint64)]),
                 "lbm_footprint_bytes": (ctypes.c_size_t, [P]),
                 "lbm_coexistence": (st, [P, _dp, _dp, _dp]),
@@ -253,6 +254,11 @@ class Domain:
         if with_gamma:
             out["gamma"] = g.reshape(self.shape)
         return out
+
+    def lbm_max_speed(self) -> float:
+        v = ctypes.c_double()
+        self._c(load().lbm_max_speed(self.handle, ctypes.byref(v)))
+        return v.value
 
     def lbm_record_gamma(self, enable=True):
         self._c(load().lbm_record_gamma(self.handle, 1 if enable else 0))

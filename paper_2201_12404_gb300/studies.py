@@ -1,0 +1,247 @@
+"""Single-relaxation-time versus entropic collision on the paper's 2-D studies.
+
+The SRT operator is the LBGK limit of the same kernels, gamma pinned to 2
+(lbm_params.gamma_mode = LBM_GAMMA_FIXED, gamma_value = 2); the entropic operator
+computes gamma per node (Sec. 2.4).  Every study is a set of D2Q9 jobs advanced
+together by persistent batched launches (lbm_batch_*), a chunk of steps at a time;
+after each chunk every job's largest speed of the reported velocity u + F/(2 rho)
+is read (lbm_max_speed, a GPU reduction), and a job whose density turns
+non-finite or non-positive, or whose speed passes a limit, is recorded as
+unstable at that chunk and leaves the batch.
+
+  spurious currents (Sec. 3.1.2): static drops, max|u| after the run, swept over
+    T/Tc at nu = 0.1, over nu at T/Tc = 0.59 and over the EOS constant a at
+    T/Tc = 0.59, with the (1 - T/Tc)^m fit of the temperature sweep;
+  stability domain (Sec. 3.2): drop impact on a film of thickness R0 (R0 = 50,
+    W = 5, nu_v = 15 nu_l, walls at the bottom and top) over a grid of liquid
+    viscosities and impact speeds.
+
+  python -m paper_2201_12404_gb300.studies spurious [--quick]
+  python -m paper_2201_12404_gb300.studies stability [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import inputs as I
+from . import lbm
+from . import workloads as WL
+
+OPERATORS = ("srt", "entropic")
+
+
+@dataclass
+class StudyJob:
+    """One D2Q9 job of a study: a workload, the EOS constant a and the operator."""
+    name: str
+    wl: WL.Workload
+    operator: str                  # "srt" (gamma = 2) or "entropic"
+    a: float = WL.PAPER_EOS["a"]
+    nu_vapour_ratio: float = 1.0   # nu_v / nu_l
+    precision: int = lbm.LBM_FP32
+    tags: dict = dataclasses.field(default_factory=dict)
+
+    def eos(self):
+        return dict(WL.PAPER_EOS, a=self.a)
+
+    def coexistence(self):
+        rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=self.wl.T_over_Tc, **self.eos()))
+        return rv, rl
+
+    def params(self, rv, rl):
+        wl = self.wl
+        bc = [0] * 6
+        if wl.walls_axis >= 0:
+            bc[2 * wl.walls_axis] = bc[2 * wl.walls_axis + 1] = 1
+        p = lbm.lbm_default_params(
+            lattice=lbm.LBM_D2Q9, precision=self.precision, nx=wl.nx, ny=wl.ny, nz=1,
+            T_over_Tc=wl.T_over_Tc, kappa=wl.kappa, nu_liquid=wl.nu_liquid,
+            nu_vapour=wl.nu_liquid * self.nu_vapour_ratio, rho_liquid=rl, rho_vapour=rv, bc=bc,
+            **self.eos())
+        if self.operator == "srt":
+            p.gamma_mode = lbm.LBM_GAMMA_FIXED
+            p.gamma_value = 2.0
+        return p
+
+
+# ---------------------------------------------------------------------------
+# Job lists (host logic only)
+# ---------------------------------------------------------------------------
+
+def static_drop(T, nu, R=40.0, side=None, kappa=0.01, W=5.0):
+    side = side or int(4 * R)
+    return WL.Workload(name=f"static drop {side}x{side} R={R:g} T/Tc={T:g} nu={nu:g}", D=2, nx=side, ny=side,
+                       nz=1, T_over_Tc=T, kappa=kappa, nu_liquid=nu, mu_ratio=0.0, R=R, U=0.0, film=0.0, W=W)
+
+
+def spurious_jobs(kind, values, R=40.0, kappa=0.01, nu=0.1, T=0.59, a=WL.PAPER_EOS["a"]):
+    """Static-drop jobs for one sweep, both operators per value.  kind: "T" (T/Tc,
+    at nu), "nu" (at T) or "a" (the EOS constant, at T and nu)."""
+    jobs = []
+    for v in values:
+        Tv, nuv, av = (v, nu, a) if kind == "T" else ((T, v, a) if kind == "nu" else (T, nu, v))
+        for op in OPERATORS:
+            jobs.append(StudyJob(name=f"{kind}={v:g} {op}", wl=static_drop(Tv, nuv, R=R, kappa=kappa), operator=op,
+                                 a=av, tags={"kind": kind, "value": v}))
+    return jobs
+
+
+def impact(nu, U, R0=50.0, T=0.59, kappa=0.01, W=5.0, width=24, height=12):
+    """The 2-D drop impact of the stability study: a drop of radius R0 at speed U over
+    a film of thickness R0 on the bottom wall, in a (width R0) x (height R0) box."""
+    return WL.Workload(name=f"impact R0={R0:g} nu={nu:g} U={U:g}", D=2, nx=int(width * R0), ny=int(height * R0),
+                       nz=1, T_over_Tc=T, kappa=kappa, nu_liquid=nu, mu_ratio=0.0, R=R0, U=U, film=1.0, W=W,
+                       walls_axis=1)
+
+
+def stability_jobs(nus, Us, R0=50.0, width=24, height=12):
+    """Drop-impact jobs over the (nu, U0) grid, both operators, nu_v = 15 nu_l."""
+    jobs = []
+    for nu in nus:
+        for U in Us:
+            for op in OPERATORS:
+                jobs.append(StudyJob(name=f"nu={nu:g} U={U:g} {op}", wl=impact(nu, U, R0=R0, width=width, height=height),
+                                     operator=op, nu_vapour_ratio=15.0, tags={"nu": nu, "U": U}))
+    return jobs
+
+
+def fit_power(x, y):
+    """Least-squares exponent m and prefactor c of y = c x^m (x, y > 0)."""
+    lx, ly = np.log(np.asarray(x, float)), np.log(np.asarray(y, float))
+    m, lc = np.polyfit(lx, ly, 1)
+    return float(m), float(math.exp(lc))
+
+
+def initial_fields(job: StudyJob, rv, rl):
+    wl = job.wl
+    if wl.U > 0 or wl.film > 0:
+        return I.drop_on_film(wl.shape, 2, wl.R, wl.film * wl.R, wl.U, rl, rv, wl.W)
+    return WL.initial_fields(wl, rv, rl)
+
+
+# ---------------------------------------------------------------------------
+# GPU execution
+# ---------------------------------------------------------------------------
+
+def run_jobs(jobs, steps, chunk=500, max_u_limit=0.5):
+    """Advance every job by up to `steps` in batched chunks.  Returns one record per
+    job: steps completed, whether it stayed stable (finite positive density and
+    max|u| below max_u_limit; u the reported velocity), the max|u| history (one
+    value per chunk) and the final max|u|; plus the batched throughput."""
+    doms, recs = [], []
+    lups, t_gpu = 0, 0.0
+    try:
+        for j in jobs:
+            rv, rl = j.coexistence()
+            d = lbm.Domain(j.params(rv, rl))
+            rho, u = initial_fields(j, rv, rl)
+            d.lbm_init_fields(rho, u)
+            doms.append(d)
+            recs.append(dict(name=j.name, operator=j.operator, tags=j.tags, rho_l=rl, rho_v=rv, steps=0, stable=True,
+                             max_u=[], final_max_u=None))
+        live = list(range(len(jobs)))
+        done = 0
+        while done < steps and live:
+            n = min(chunk, steps - done)
+            t0 = time.perf_counter()
+            with lbm.Batch([doms[k] for k in live]) as b:
+                b.lbm_batch_step(n)
+                try:
+                    b.lbm_batch_synchronize()
+                except lbm.LBMError:
+                    pass  # the failing jobs are found below
+            t_gpu += time.perf_counter() - t0
+            lups += n * sum(jobs[k].wl.N for k in live)
+            done += n
+            still = []
+            for k in live:
+                r = recs[k]
+                try:
+                    doms[k].lbm_synchronize()
+                    mu = doms[k].lbm_max_speed()
+                except lbm.LBMError:
+                    mu = float("nan")
+                r["max_u"].append(mu)
+                if not (mu == mu) or mu > max_u_limit:
+                    r["stable"] = False
+                    r["failed_at"] = done
+                    r["failure"] = "speed limit" if mu == mu and mu != float("inf") else "non-finite"
+                else:
+                    r["steps"] = done
+                    r["final_max_u"] = mu
+                    still.append(k)
+            live = still
+        return dict(jobs=recs, steps=steps, chunk=chunk, batched_mlups=lups / max(t_gpu, 1e-9) / 1e6)
+    finally:
+        for d in doms:
+            d.close()
+
+
+def spurious_study(quick=False):
+    """The three spurious-current sweeps and the temperature exponent."""
+    if quick:
+        Ts, nus, As, R, steps = (0.59, 0.8), (0.01, 0.1), (0.003, 0.0017), 20.0, 2000
+    else:
+        Ts = (0.5, 0.55, 0.59, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95)
+        nus = (0.001, 0.0025, 0.005, 0.01, 0.02, 0.03, 0.05, 0.1)
+        As = (0.003, 0.0017, 0.0011)
+        R, steps = 40.0, 20000
+    out = {}
+    for kind, vals in (("T", Ts), ("nu", nus), ("a", As)):
+        res = run_jobs(spurious_jobs(kind, vals, R=R), steps, chunk=max(500, steps // 20))
+        rows = []
+        for v in vals:
+            row = {"value": v}
+            for r in res["jobs"]:
+                if r["tags"]["value"] == v:
+                    row[r["operator"]] = r["final_max_u"] if r["stable"] else None
+                    row[r["operator"] + "_history"] = r["max_u"]
+            rows.append(row)
+        out[kind] = dict(rows=rows, steps=steps, batched_mlups=res["batched_mlups"])
+    for op in OPERATORS:
+        pts = [(1 - r["value"], r[op]) for r in out["T"]["rows"] if r.get(op)]
+        if len(pts) >= 2:
+            out["T"][f"m_{op}"] = fit_power([p[0] for p in pts], [p[1] for p in pts])[0]
+    return out
+
+
+def stability_study(quick=False):
+    """The (nu, U0) stability domain of both operators."""
+    if quick:
+        nus, Us, R0, steps = (0.005, 0.05), (0.0, 0.08), 20.0, 2000
+    else:
+        nus = (0.0025, 0.005, 0.01, 0.02, 0.03, 0.04, 0.06, 0.1)
+        Us = (0.0, 0.04, 0.08, 0.12, 0.16)
+        R0, steps = 50.0, 5000
+    res = run_jobs(stability_jobs(nus, Us, R0=R0), steps, chunk=500)
+    table = {op: {f"{nu:g}": {f"{U:g}": None for U in Us} for nu in nus} for op in OPERATORS}
+    for r in res["jobs"]:
+        table[r["operator"]][f"{r['tags']['nu']:g}"][f"{r['tags']['U']:g}"] = (
+            "stable" if r["stable"] else f"{r['failure']}@{r['failed_at']}")
+    lowest = {}
+    for op in OPERATORS:
+        ok = [nu for nu in nus if all(table[op][f"{nu:g}"][f"{U:g}"] == "stable" for U in Us)]
+        lowest[op] = min(ok) if ok else None
+    return dict(R0=R0, steps=steps, nus=list(nus), Us=list(Us), table=table,
+                lowest_nu_stable_for_all_U=lowest, batched_mlups=res["batched_mlups"])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=["spurious", "stability"])
+    ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
+    args = ap.parse_args()
+    lbm.load()
+    res = spurious_study(args.quick) if args.study == "spurious" else stability_study(args.quick)
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -19,6 +19,7 @@ JOBS = [
     dict(D=2, nx=33, ny=70, Tr=0.9),
     dict(D=2, nx=130, ny=29, Tr=0.6, walls=True, kappa=0.005),
     dict(D=2, nx=5, ny=5, Tr=0.8, kappa=0.0),
+    dict(D=2, nx=48, ny=40, Tr=0.7, gamma_mode=1, gamma_value=2.0),  # SRT (LBGK limit) job
 ]
 
 

@@ -1,0 +1,57 @@
+"""SRT-versus-entropic study runner on the GPU, at small sizes: every job of a
+batched study runs, the stable ones report finite velocities below the
+instability limit, and a job that blows up leaves the batch while the others go on."""
+import math
+
+import pytest
+
+from paper_2201_12404_gb300 import studies as S
+
+pytestmark = pytest.mark.gpu
+
+
+def test_small_spurious_sweep_runs_both_operators_batched():
+    jobs = S.spurious_jobs("T", (0.6, 0.8), R=10.0)
+    res = S.run_jobs(jobs, steps=600, chunk=200)
+    assert len(res["jobs"]) == 4 and res["batched_mlups"] > 0
+    for r in res["jobs"]:
+        assert r["stable"] and r["steps"] == 600 and len(r["max_u"]) == 3
+        assert 0 < r["final_max_u"] < 0.5 and all(math.isfinite(v) for v in r["max_u"])
+
+
+def test_unstable_job_leaves_the_batch_and_the_rest_continue():
+    """An SRT impact at a viscosity far below its stability limit fails; the static
+    drop beside it in the same batch keeps running to the end."""
+    bad = S.stability_jobs((1e-5,), (0.16,), R0=12.0)[0]
+    assert bad.operator == "srt"
+    good = S.spurious_jobs("T", (0.8,), R=10.0)[1]
+    res = S.run_jobs([bad, good], steps=3000, chunk=500)
+    rb, rg = res["jobs"]
+    assert not rb["stable"] and rb["failed_at"] <= 3000
+    assert rg["stable"] and rg["steps"] == 3000
+
+
+def test_max_speed_is_the_largest_reported_velocity():
+    """lbm_max_speed reduces |u + F/(2 rho)| on the GPU: in float64 it equals the
+    largest speed of the oracle's reported velocity (reading R11) and, in float32,
+    of the field lbm_read_macroscopic returns."""
+    import numpy as np
+
+    import oracle as O
+    from cases import case, drop_state, lbm_params, oracle_params
+    from paper_2201_12404_gb300 import lbm
+    c = case(2, 40, 30, Tr=0.7, g=(1e-5, 0.0, 0.0))
+    f0 = drop_state(c)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(f0)
+        v = dom.lbm_max_speed()
+    _, u_o = O.macroscopic(oracle_params(c), f0)
+    ref = float(np.max(np.sqrt(np.sum(np.asarray(u_o).reshape(2, -1) ** 2, axis=0))))
+    assert v == pytest.approx(ref, rel=1e-12)
+    c32 = case(3, 20, 14, 12, Tr=0.7, precision=lbm.LBM_FP32)
+    with lbm.Domain(lbm_params(c32)) as dom:
+        dom.lbm_write_populations(drop_state(c32).astype(np.float32).astype(np.float64))
+        dom.lbm_step(3)
+        v = dom.lbm_max_speed()
+        _, u = dom.lbm_read_macroscopic()
+    assert v == pytest.approx(float(np.max(np.sqrt(np.sum(u.reshape(3, -1) ** 2, axis=0)))), rel=1e-12)

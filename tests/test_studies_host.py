@@ -1,0 +1,44 @@
+"""Host logic of the SRT-versus-entropic studies (no GPU): job lists, operator
+parameters and the power-law fit."""
+import pytest
+
+from paper_2201_12404_gb300 import lbm
+from paper_2201_12404_gb300 import studies as S
+
+
+def test_spurious_sweeps_pair_every_value_with_both_operators():
+    for kind, vals in (("T", (0.5, 0.7, 0.9)), ("nu", (0.001, 0.1)), ("a", (0.003, 0.0011))):
+        jobs = S.spurious_jobs(kind, vals)
+        assert len(jobs) == 2 * len(vals)
+        for v in vals:
+            ops = sorted(j.operator for j in jobs if j.tags["value"] == v)
+            assert ops == ["entropic", "srt"]
+    j = S.spurious_jobs("a", (0.0011,))[0]
+    assert j.a == 0.0011 and j.wl.T_over_Tc == 0.59 and j.wl.nu_liquid == 0.1
+    j = S.spurious_jobs("T", (0.8,))[0]
+    assert j.wl.T_over_Tc == 0.8 and j.wl.U == 0 and j.wl.walls_axis == -1
+
+
+def test_srt_is_gamma_pinned_to_two_and_entropic_is_not():
+    srt, ent = S.spurious_jobs("T", (0.8,))
+    assert srt.operator == "srt"
+    p = srt.params(0.2, 7.2)
+    assert p.gamma_mode == lbm.LBM_GAMMA_FIXED and p.gamma_value == 2.0
+    assert ent.params(0.2, 7.2).gamma_mode == lbm.LBM_GAMMA_ENTROPIC
+
+
+def test_stability_jobs_follow_the_paper_setup():
+    jobs = S.stability_jobs((0.005, 0.04), (0.0, 0.16), R0=50.0)
+    assert len(jobs) == 8
+    wl = jobs[0].wl
+    assert (wl.nx, wl.ny) == (1200, 600) and wl.R == 50.0 and wl.W == 5.0 and wl.walls_axis == 1
+    assert wl.film * wl.R == 50.0  # film thickness R0
+    p = jobs[0].params(0.0083, 8.78)
+    assert p.nu_vapour == pytest.approx(15 * p.nu_liquid)
+    assert p.bc[2] == lbm.LBM_BC_BOUNCEBACK and p.bc[3] == lbm.LBM_BC_BOUNCEBACK and p.bc[0] == lbm.LBM_BC_PERIODIC
+
+
+def test_power_fit_recovers_exponent_and_prefactor():
+    xs = [0.05, 0.1, 0.2, 0.41]
+    m, c = S.fit_power(xs, [3e-4 * x ** 2.2 for x in xs])
+    assert m == pytest.approx(2.2, abs=1e-12) and c == pytest.approx(3e-4, rel=1e-12)
