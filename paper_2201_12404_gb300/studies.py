@@ -14,10 +14,15 @@ unstable at that chunk and leaves the batch.
     T/Tc = 0.59, with the (1 - T/Tc)^m fit of the temperature sweep;
   stability domain (Sec. 3.2): drop impact on a film of thickness R0 (R0 = 50,
     W = 5, nu_v = 15 nu_l, walls at the bottom and top) over a grid of liquid
-    viscosities and impact speeds.
+    viscosities and impact speeds;
+  surface tension (Sec. 3.1.2, Eq. Laplace_equimolar): static drops of three radii
+    per temperature (entropic operator), sigma from the pressure jump against the
+    equimolar radius, and the exponents of sigma ~ (1 - T/Tc)^m above and below
+    T/Tc = 0.8 (the paper: 3/2 and 11/9).
 
   python -m paper_2201_12404_gb300.studies spurious [--quick]
   python -m paper_2201_12404_gb300.studies stability [--quick]
+  python -m paper_2201_12404_gb300.studies surface-tension [--quick]
 """
 from __future__ import annotations
 
@@ -130,11 +135,12 @@ def initial_fields(job: StudyJob, rv, rl):
 # GPU execution
 # ---------------------------------------------------------------------------
 
-def run_jobs(jobs, steps, chunk=500, max_u_limit=0.5):
+def run_jobs(jobs, steps, chunk=500, max_u_limit=0.5, keep_density=False):
     """Advance every job by up to `steps` in batched chunks.  Returns one record per
     job: steps completed, whether it stayed stable (finite positive density and
     max|u| below max_u_limit; u the reported velocity), the max|u| history (one
-    value per chunk) and the final max|u|; plus the batched throughput."""
+    value per chunk) and the final max|u| (with keep_density, the final density
+    field of every stable job too); plus the batched throughput."""
     doms, recs = [], []
     lups, t_gpu = 0, 0.0
     try:
@@ -178,10 +184,103 @@ def run_jobs(jobs, steps, chunk=500, max_u_limit=0.5):
                     r["final_max_u"] = mu
                     still.append(k)
             live = still
+        if keep_density:
+            for k in live:
+                recs[k]["rho"] = doms[k].lbm_read_macroscopic()[0][0]
         return dict(jobs=recs, steps=steps, chunk=chunk, batched_mlups=lups / max(t_gpu, 1e-9) / 1e6)
     finally:
         for d in doms:
             d.close()
+
+
+def pr_pressure(rho, T, a=WL.PAPER_EOS["a"], b=WL.PAPER_EOS["b"], R=WL.PAPER_EOS["R"], acentric=WL.PAPER_EOS["acentric"]):
+    """Peng-Robinson pressure (Eq. PREoS) at reduced temperature T."""
+    Tc = 0.0778 * a / (0.45724 * b * R)
+    m = 0.37464 + 1.54226 * acentric - 0.26992 * acentric ** 2
+    al = (1 + m * (1 - math.sqrt(T))) ** 2
+    return rho * R * T * Tc / (1 - b * rho) - a * al * rho ** 2 / (1 + 2 * b * rho - b * b * rho ** 2)
+
+
+def interface_width(rho, rho_in, rho_out):
+    """W = (rho_l - rho_v) / max |grad rho| (the paper's interface thickness),
+    central differences on the periodic 2-D field."""
+    gy = 0.5 * (np.roll(rho, -1, 0) - np.roll(rho, 1, 0))
+    gx = 0.5 * (np.roll(rho, -1, 1) - np.roll(rho, 1, 1))
+    return float(abs(rho_in - rho_out) / np.max(np.hypot(gx, gy)))
+
+
+def laplace_measure(rho, R0):
+    """Pressure-jump inputs of a 2-D drop centred in its box: the equimolar radius
+    R_e (the disc that holds the excess mass at the bulk jump), the interface width
+    W, and the bulk densities inside (r < R_e - 4W) and outside (r > R_e + 4W).
+    Starts from the initial radius R0 and refines once with the measured R_e, W."""
+    ny, nx = rho.shape
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.hypot(xx - nx / 2, yy - ny / 2)
+    r_out = float(np.mean(rho[r > R0 + 12]))
+    r_in = float(np.mean(rho[r < R0 / 2]))
+    Re, W = R0, 0.0
+    for _ in range(2):
+        Re = math.sqrt(float(np.sum(rho - r_out)) / (math.pi * (r_in - r_out)))
+        W = interface_width(rho, r_in, r_out)
+        inner, outer = r < max(Re - 4 * W, Re / 4), r > Re + 4 * W
+        if outer.any():
+            r_out = float(np.mean(rho[outer]))
+        r_in = float(np.mean(rho[inner]))
+    return r_in, r_out, Re, W
+
+
+def surface_tension_jobs(Ts, radii, kappa=0.01, nu=0.1, radii_near_tc=None, t_near=0.85):
+    """Static drops, entropic operator: every radius at every temperature (radii_near_tc
+    instead at T/Tc >= t_near, where the interface is wider)."""
+    jobs = []
+    for T in Ts:
+        for R in (radii_near_tc if (radii_near_tc and T >= t_near - 1e-12) else radii):
+            jobs.append(StudyJob(name=f"T={T:g} R={R:g}", wl=static_drop(T, nu, R=R, kappa=kappa), operator="entropic",
+                                 tags={"T": T, "R": R}))
+    return jobs
+
+
+def surface_tension_study(quick=False):
+    """sigma(T) from the Laplace law at three radii per temperature, and the exponents."""
+    if quick:
+        groups = [((0.6, 0.75), (25.0, 40.0), 3000)]
+    else:
+        # near the critical point the interface is wider (R0/W > 10 needs larger drops)
+        # and the drops take longer to settle at their Laplace-shifted densities
+        groups = [((0.5, 0.55, 0.6, 0.65, 0.7, 0.75, 0.8), (30.0, 45.0, 60.0), 20000),
+                  ((0.85, 0.9, 0.95), (120.0, 160.0, 200.0), 100000)]
+    Ts, jobs_out, lups_s = [], [], []
+    for g_Ts, g_radii, g_steps in groups:
+        r = run_jobs(surface_tension_jobs(g_Ts, g_radii), g_steps, chunk=max(500, g_steps // 10), keep_density=True)
+        for j in r["jobs"]:
+            j["steps_run"] = g_steps
+        Ts += list(g_Ts)
+        jobs_out += r["jobs"]
+        lups_s.append(r["batched_mlups"])
+    res = dict(jobs=jobs_out, batched_mlups=min(lups_s))
+    rows = []
+    for T in Ts:
+        pts = []
+        for r in res["jobs"]:
+            if r["tags"]["T"] == T and r["stable"]:
+                r_in, r_out, Re, W = laplace_measure(r["rho"], r["tags"]["R"])
+                dP = pr_pressure(r_in, T) - pr_pressure(r_out, T)
+                pts.append(dict(R0=r["tags"]["R"], R_e=Re, W=W, rho_in=r_in, rho_out=r_out, dP=dP, dP_Re=dP * Re,
+                                max_u=r["final_max_u"], steps=r["steps_run"]))
+        row = dict(T_over_Tc=T, drops=pts)
+        if len(pts) >= 2:
+            # Delta P = sigma / R_e (2-D): slope of Delta P against 1/R_e
+            slope, icpt = np.polyfit([1 / p["R_e"] for p in pts], [p["dP"] for p in pts], 1)
+            row.update(sigma=float(slope), intercept=float(icpt))
+        rows.append(row)
+    out = dict(groups=[dict(T_over_Tc=list(g[0]), radii=list(g[1]), steps=g[2]) for g in groups], rows=rows,
+               batched_mlups=res["batched_mlups"])
+    for name, lo, hi in (("m_near_critical", 0.8, 1.0), ("m_below_0.8", 0.0, 0.8 + 1e-9)):
+        pts = [(1 - r["T_over_Tc"], r["sigma"]) for r in rows if "sigma" in r and r["sigma"] > 0 and lo <= r["T_over_Tc"] < hi]
+        if len(pts) >= 2:
+            out[name] = fit_power([p[0] for p in pts], [p[1] for p in pts])[0]
+    return out
 
 
 def spurious_study(quick=False):
@@ -235,11 +334,12 @@ def stability_study(quick=False):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["spurious", "stability"])
+    ap.add_argument("study", choices=["spurious", "stability", "surface-tension"])
     ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
     args = ap.parse_args()
     lbm.load()
-    res = spurious_study(args.quick) if args.study == "spurious" else stability_study(args.quick)
+    res = {"spurious": spurious_study, "stability": stability_study,
+           "surface-tension": surface_tension_study}[args.study](args.quick)
     print(json.dumps(res), flush=True)
 
 

@@ -55,3 +55,10 @@ def test_max_speed_is_the_largest_reported_velocity():
         v = dom.lbm_max_speed()
         _, u = dom.lbm_read_macroscopic()
     assert v == pytest.approx(float(np.max(np.sqrt(np.sum(u.reshape(3, -1) ** 2, axis=0)))), rel=1e-12)
+
+
+def test_quick_surface_tension_sweep_gives_positive_sigma_falling_towards_tc():
+    res = S.surface_tension_study(quick=True)
+    sig = {r["T_over_Tc"]: r.get("sigma") for r in res["rows"]}
+    assert sig[0.6] is not None and sig[0.75] is not None
+    assert sig[0.6] > sig[0.75] > 0

@@ -42,3 +42,28 @@ def test_power_fit_recovers_exponent_and_prefactor():
     xs = [0.05, 0.1, 0.2, 0.41]
     m, c = S.fit_power(xs, [3e-4 * x ** 2.2 for x in xs])
     assert m == pytest.approx(2.2, abs=1e-12) and c == pytest.approx(3e-4, rel=1e-12)
+
+
+def test_laplace_measure_on_a_sharp_disc_and_the_pressure_law():
+    """A step disc of radius 20 (densities 8 and 0.5) gives back its radius and bulk
+    densities; the pressure is the Peng-Robinson law (ideal-gas limit at low density)."""
+    import numpy as np
+    n = 100
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    rho = np.where(np.hypot(xx - n / 2, yy - n / 2) < 20.0, 8.0, 0.5)
+    r_in, r_out, Re, W = S.laplace_measure(rho, 20.0)
+    assert r_in == 8.0 and r_out == 0.5 and Re == pytest.approx(20.0, rel=0.01)
+    # a step of 7.5: central differences of 3.75 in both directions where the step
+    # runs diagonally, max |grad rho| = 3.75 sqrt 2, W = sqrt 2
+    assert W == pytest.approx(2 ** 0.5)
+    T = 0.8
+    Tc = 0.0778 * 0.003 / (0.45724 * 0.095)
+    assert S.pr_pressure(1e-9, T) == pytest.approx(1e-9 * T * Tc, rel=1e-6)
+
+
+def test_surface_tension_jobs_cover_every_temperature_and_radius():
+    jobs = S.surface_tension_jobs((0.6, 0.9), (30.0, 45.0, 60.0), radii_near_tc=(60.0, 90.0, 120.0))
+    assert len(jobs) == 6 and all(j.operator == "entropic" for j in jobs)
+    assert {(j.tags["T"], j.tags["R"]) for j in jobs} == {(0.6, r) for r in (30.0, 45.0, 60.0)} | {
+        (0.9, r) for r in (60.0, 90.0, 120.0)}
+    assert jobs[0].wl.nx == 120 and jobs[-1].wl.nx == 480
