@@ -161,6 +161,27 @@ lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* 
  * one reduction.  A state with a non-finite speed gives +inf.  Synchronising. */
 lbm_status lbm_max_speed(lbm_handle h, double* max_u);
 
+/* Interface thickness W = (rho_liquid - rho_vapour) / max |grad rho| of the
+ * current state (Sec. 3.1.1), rho_liquid and rho_vapour those of the domain's
+ * parameters, the gradient by second-order central differences (across periodic
+ * wraps and mirrored at walls), the maximum reduced on the GPU; +inf for a uniform
+ * state.  max_grad (nullable) receives max |grad rho|.  Synchronising. */
+lbm_status lbm_interface_width(lbm_handle h, double* width, double* max_grad);
+
+/* Crown (spreading) radius of a drop impact (Sec. 3.2): over the nodes of layer
+ * `layer` (index along the last axis: y in 2-D, z in 3-D), the largest distance
+ * from the vertical axis through the domain centre (x = (nx-1)/2 [, y = (ny-1)/2])
+ * of a node whose density exceeds (rho_liquid + rho_vapour)/2; 0 when none does.
+ * Reduced on the GPU.  LBM_ERR_INVALID_ARG for a layer outside the domain.
+ * Synchronising. */
+lbm_status lbm_crown_radius(lbm_handle h, int32_t layer, double* radius);
+
+/* 2/(omega gamma) per node (N values, x fastest) of the last step run with gamma
+ * recording on, omega the node's relaxation rate in that step: about 1 where the
+ * entropic stabiliser is idle, away from the interfaces (Sec. 3.3).
+ * LBM_ERR_INVALID_ARG when no step has been recorded.  Synchronising. */
+lbm_status lbm_read_relaxation(lbm_handle h, double* two_over_omega_gamma);
+
 /* Turn per-node gamma recording on (enable != 0) or off for later lbm_step
  * calls.  Recording adds a float32 store per node and step (the 2/(omega gamma)
  * field of Sec. 3.3 is derived from it). */

@@ -215,6 +215,27 @@ double bisect_p(const EosCoeffs& e, double target, double lo, double hi) {
   return 0.5 * (lo + hi);
 }
 
+// Pass 1 for the current state, then a block-partial maximum (field 4 of the
+// [block][5] layout, at most N blocks) reduced by diag_final_kernel; *out = the maximum.
+template <typename Partial>
+lbm_status reduce_max(lbm_handle h, Partial partial, double* out) {
+  lbm_status st = refresh_aux(h);
+  if (st != LBM_OK) return st;
+  const long long nblk = (h->dev.N + 255) / 256;
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)(nblk * 5 + 5) * sizeof(double), h->stream));
+  const int nb = partial(buf);
+  lbm::launch_diag_final(buf, nb, buf + nblk * 5, h->stream);
+  h->launches += 2;
+  LBM_CUDA(h, cudaGetLastError());
+  double res[5];
+  LBM_CUDA(h, cudaMemcpyAsync(res, buf + nblk * 5, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = res[4];
+  return LBM_OK;
+}
+
 }  // namespace
 
 lbm_status lbm_internal_enqueue_flag_copy(lbm_domain* h, cudaStream_t stream) {
@@ -416,9 +437,11 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
   lbm_status st = poll_flags(h, false);
   if (st != LBM_OK) return st;
   if (h->record_gamma && !h->dev.gamma_out) {
-    LBM_CUDA(h, cudaMalloc(&h->dev.gamma_out, (size_t)h->dev.N * sizeof(float)));
-    LBM_CUDA(h, cudaMemsetAsync(h->dev.gamma_out, 0, (size_t)h->dev.N * sizeof(float), h->stream));
+    // (gamma, omega) per node
+    LBM_CUDA(h, cudaMalloc(&h->dev.gamma_out, 2 * (size_t)h->dev.N * sizeof(float)));
+    LBM_CUDA(h, cudaMemsetAsync(h->dev.gamma_out, 0, 2 * (size_t)h->dev.N * sizeof(float), h->stream));
   }
+  if (h->record_gamma && nsteps > 0) h->gamma_recorded = true;
   DevDomain saved = h->dev;
   if (!h->record_gamma) h->dev.gamma_out = nullptr;
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -512,9 +535,9 @@ lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* 
   if (max_u) *max_u = out[4];
   if (gamma_field) {
     if (h->dev.gamma_out) {
-      std::vector<float> g((size_t)h->dev.N);
+      std::vector<float> g(2 * (size_t)h->dev.N);
       LBM_CUDA(h, cudaMemcpy(g.data(), h->dev.gamma_out, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
-      for (size_t k = 0; k < g.size(); ++k) gamma_field[k] = g[k];
+      for (long long k = 0; k < h->dev.N; ++k) gamma_field[k] = g[2 * k];
     } else {
       for (long long k = 0; k < h->dev.N; ++k) gamma_field[k] = 0.0;
     }
@@ -525,20 +548,38 @@ lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* 
 lbm_status lbm_max_speed(lbm_handle h, double* max_u) {
   LBM_LIVE(h);
   if (!max_u) return fail(h, LBM_ERR_INVALID_ARG, "max_u is NULL");
-  lbm_status st = refresh_aux(h);
+  return reduce_max(h, [&](double* buf) { return h->ops->max_speed_partial(h->dev, h->parity, buf, h->stream); }, max_u);
+}
+
+lbm_status lbm_interface_width(lbm_handle h, double* width, double* max_grad) {
+  LBM_LIVE(h);
+  if (!width) return fail(h, LBM_ERR_INVALID_ARG, "width is NULL");
+  double g = 0;
+  const lbm_status st = reduce_max(h, [&](double* buf) { return h->ops->grad_partial(h->dev, buf, h->stream); }, &g);
   if (st != LBM_OK) return st;
-  const long long nblk = (h->dev.N + 255) / 256;
-  double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)(nblk * 5 + 5) * sizeof(double), h->stream));
-  int nb = h->ops->max_speed_partial(h->dev, h->parity, buf, h->stream);
-  lbm::launch_diag_final(buf, nb, buf + nblk * 5, h->stream);
-  h->launches += 2;
-  LBM_CUDA(h, cudaGetLastError());
-  double out[5];
-  LBM_CUDA(h, cudaMemcpyAsync(out, buf + nblk * 5, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
-  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  *width = g > 0 ? (h->p.rho_liquid - h->p.rho_vapour) / g : INFINITY;
+  if (max_grad) *max_grad = g;
+  return LBM_OK;
+}
+
+lbm_status lbm_crown_radius(lbm_handle h, int32_t layer, double* radius) {
+  LBM_LIVE(h);
+  if (!radius) return fail(h, LBM_ERR_INVALID_ARG, "radius is NULL");
+  const int last = h->dev.pz > 1 ? h->dev.nz : h->dev.ny;
+  if (layer < 0 || layer >= last) return fail(h, LBM_ERR_INVALID_ARG, "layer outside the domain's last axis");
+  const double mid = 0.5 * (h->p.rho_liquid + h->p.rho_vapour);
+  return reduce_max(h, [&](double* buf) { return h->ops->crown_partial(h->dev, layer, mid, buf, h->stream); }, radius);
+}
+
+lbm_status lbm_read_relaxation(lbm_handle h, double* two_over_omega_gamma) {
+  LBM_LIVE(h);
+  if (!two_over_omega_gamma) return fail(h, LBM_ERR_INVALID_ARG, "output is NULL");
+  if (!h->dev.gamma_out || !h->gamma_recorded)
+    return fail(h, LBM_ERR_INVALID_ARG, "no step has run with gamma recording on (lbm_record_gamma)");
+  std::vector<float> g(2 * (size_t)h->dev.N);
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-  *max_u = out[4];
+  LBM_CUDA(h, cudaMemcpy(g.data(), h->dev.gamma_out, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  for (long long k = 0; k < h->dev.N; ++k) two_over_omega_gamma[k] = 2.0 / ((double)g[2 * k + 1] * (double)g[2 * k]);
   return LBM_OK;
 }
 

@@ -542,7 +542,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   } else {
     gamma = entropic_gamma<R>(sA, sB, om);
   }
-  if (d.gamma_out) d.gamma_out[n] = (float)gamma;
+  if (d.gamma_out) ((float2*)d.gamma_out)[n] = make_float2((float)gamma, (float)om);
 
   // ---- pass B: f' = g - (omega gamma/2) h
   const R ch = (R)0.5 * om * gamma;

@@ -82,7 +82,7 @@ __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return double2{a
 struct DevDomain {
   void* f;             // populations (storage type)
   void* aux;           // padded auxiliary fields (float64 in the FP64 path, float32 otherwise)
-  float* gamma_out;    // per-node gamma of the last step, or nullptr
+  float* gamma_out;    // per-node (gamma, omega) pairs of the last step, or nullptr
   unsigned int* flags; // bit 0: non-finite or non-positive density seen
   unsigned long long* guards; // nodes where f*_i <= 0 forced gamma = 2
   long long N, PN;     // interior and padded node counts

@@ -34,6 +34,7 @@ struct lbm_domain {
   double ms[2] = {0, 0};
   int64_t cnt[2] = {0, 0};
   bool record_gamma = false;
+  bool gamma_recorded = false;  // a step has run with recording on since the buffer was made
 };
 
 // Mark the domain's error word as copied to the host after work enqueued on `stream`

@@ -94,10 +94,20 @@ struct Launch {
     max_speed_partial_kernel<D, S, R, A><<<blocks1d(d), 256, 0, s>>>(d, parity, partial);
     return (int)blocks1d(d);
   }
+  static int grad_partial(const DevDomain& d, double* partial, cudaStream_t s) {
+    grad_partial_kernel<D, A><<<blocks1d(d), 256, 0, s>>>(d, partial);
+    return (int)blocks1d(d);
+  }
+  static int crown_partial(const DevDomain& d, int layer, double rho_mid, double* partial, cudaStream_t s) {
+    const long long nl = D == 3 ? (long long)d.nx * d.ny : d.nx;
+    const unsigned nb = (unsigned)((nl + 255) / 256);
+    crown_partial_kernel<D, A><<<nb, 256, 0, s>>>(d, layer, rho_mid, partial);
+    return (int)nb;
+  }
   static Ops table() {
     return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
                &canonical_read, &canonical_write, &macroscopic, &bare_velocity, &diag_partial,
-               &max_speed_partial};
+               &max_speed_partial, &grad_partial, &crown_partial};
   }
 };
 

@@ -239,6 +239,74 @@ __global__ void __launch_bounds__(256) max_speed_partial_kernel(DevDomain d, int
 }
 
 // ---------------------------------------------------------------------------
+// Largest |grad rho| of the auxiliary density (second-order central differences;
+// the ghost layer supplies the wrapped or mirrored neighbours), one partial
+// maximum per block in field 4 of the diag layout.
+// ---------------------------------------------------------------------------
+template <int D, typename A>
+__global__ void __launch_bounds__(256) grad_partial_kernel(DevDomain d, double* partial) {
+  __shared__ double sh[256];
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double gm = 0;
+  if (n < d.N) {
+    const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+    const Two<A>* a2 = (const Two<A>*)d.aux;
+    const long long pc = pnode_of<D>(d, x, y, z);
+    const long long e[3] = {1, d.px, (long long)d.px * d.py};
+    double g2 = 0;
+    for (int a = 0; a < D; ++a) {
+      const double ga = 0.5 * ((double)a2[pc + e[a]].x - (double)a2[pc - e[a]].x);
+      g2 += ga * ga;
+    }
+    gm = sqrt(g2);
+  }
+  sh[threadIdx.x] = gm;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) partial[blockIdx.x * 5 + k] = 0.0;
+    partial[blockIdx.x * 5 + 4] = sh[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Crown radius: over the nodes of one layer (index `layer` along the last axis),
+// the largest distance from the vertical axis through the domain centre of a
+// node whose auxiliary density exceeds rho_mid; one partial maximum per block in
+// field 4 of the diag layout (0 where no node qualifies).
+// ---------------------------------------------------------------------------
+template <int D, typename A>
+__global__ void __launch_bounds__(256) crown_partial_kernel(DevDomain d, int layer, double rho_mid, double* partial) {
+  __shared__ double sh[256];
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nl = D == 3 ? (long long)d.nx * d.ny : d.nx;
+  double rm = 0;
+  if (k < nl) {
+    const int x = (int)(k % d.nx);
+    const int y = D == 3 ? (int)(k / d.nx) : layer;
+    const int z = D == 3 ? layer : 0;
+    const Two<A>* a2 = (const Two<A>*)d.aux;
+    if ((double)a2[pnode_of<D>(d, x, y, z)].x > rho_mid) {
+      const double dx = x - 0.5 * (d.nx - 1), dy = D == 3 ? y - 0.5 * (d.ny - 1) : 0.0;
+      rm = sqrt(dx * dx + dy * dy);
+    }
+  }
+  sh[threadIdx.x] = rm;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) partial[blockIdx.x * 5 + q] = 0.0;
+    partial[blockIdx.x * 5 + 4] = sh[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Bare velocity of a state at rest in the reported sense: u -= F dt/(2 rho) in
 // place, F from the auxiliary fields of the current (equilibrium) state.
 // ---------------------------------------------------------------------------

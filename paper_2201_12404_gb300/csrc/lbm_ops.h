@@ -25,6 +25,10 @@ struct Ops {
   int (*diag_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
   // the same layout, field 4 = largest |u + F/(2 rho)| of the block (auxiliary fields current)
   int (*max_speed_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
+  // the same layout, field 4 = largest |grad rho| of the block (auxiliary fields current)
+  int (*grad_partial)(const DevDomain&, double* partial, cudaStream_t);
+  // the same layout, field 4 = crown radius of the block's nodes of one layer
+  int (*crown_partial)(const DevDomain&, int layer, double rho_mid, double* partial, cudaStream_t);
 };
 
 // Defined in lbm_d2q9.cu and lbm_d3q27.cu.

@@ -85,6 +85,9 @@ def load():
                 "lbm_read_diag": (st, [H, _dp, _dp, _dp, _dp]),
                 "lbm_record_gamma": (st, [H, ctypes.c_int]),
                 "lbm_max_speed": (st, [H, _dp]),
+                "lbm_interface_width": (st, [H, _dp, _dp]),
+                "lbm_crown_radius": (st, [H, ctypes.c_int32, _dp]),
+                "lbm_read_relaxation": (st, [H, _dp]),
                 "lbm_guard_count": (st, [H, ctypes.POINTER(ctypes.c_uint64)]),
                 "lbm_footprint_bytes": (ctypes.c_size_t, [P]),
                 "lbm_coexistence": (st, [P, _dp, _dp, _dp]),
@@ -259,6 +262,22 @@ class Domain:
         v = ctypes.c_double()
         self._c(load().lbm_max_speed(self.handle, ctypes.byref(v)))
         return v.value
+
+    def lbm_interface_width(self):
+        """(W, max |grad rho|) of the current state."""
+        w, g = ctypes.c_double(), ctypes.c_double()
+        self._c(load().lbm_interface_width(self.handle, ctypes.byref(w), ctypes.byref(g)))
+        return w.value, g.value
+
+    def lbm_crown_radius(self, layer: int) -> float:
+        r = ctypes.c_double()
+        self._c(load().lbm_crown_radius(self.handle, int(layer), ctypes.byref(r)))
+        return r.value
+
+    def lbm_read_relaxation(self):
+        out = np.empty(self.N)
+        self._c(load().lbm_read_relaxation(self.handle, _ptr(out)))
+        return out.reshape(self.shape)
 
     def lbm_record_gamma(self, enable=True):
         self._c(load().lbm_record_gamma(self.handle, 1 if enable else 0))

@@ -23,6 +23,13 @@ unstable at that chunk and leaves the batch.
   python -m paper_2201_12404_gb300.studies spurious [--quick]
   python -m paper_2201_12404_gb300.studies stability [--quick]
   python -m paper_2201_12404_gb300.studies surface-tension [--quick]
+
+and, for the entropic operator alone, the crown radius of the 2-D drop impact
+(Sec. 3.2) sampled on the GPU (lbm_crown_radius, the layer just above the film)
+with the fit r ~ (t - t0)^p over the first convective time after contact (the
+paper: p = 1/2), and the 2/(omega gamma) field of its last step (Sec. 3.3):
+
+  python -m paper_2201_12404_gb300.studies crown [--quick]
 """
 from __future__ import annotations
 
@@ -283,6 +290,51 @@ def surface_tension_study(quick=False):
     return out
 
 
+def crown_study(quick=False, wl=None, t_end_tau=2.0, samples=100, precision=lbm.LBM_FP32):
+    """Crown radius r(t) of a 2-D drop impact (entropic operator), sampled on the
+    GPU in the layer y = h + 2 above the film, the exponent p of r ~ (t - t0)^p over
+    0.05 tau <= t - t0 <= tau (t0 = first sample with a crown, tau = 2R/U), and the
+    2/(omega gamma) field of the last step: its share of nodes within 5% of 1 and
+    the same share at interface nodes (0.1 < phase fraction < 0.9)."""
+    if wl is None:
+        wl = WL.DROP_IMPACT_2D if not quick else dataclasses.replace(
+            WL.DROP_IMPACT_2D, name="D2Q9 drop impact 512x256 (R = 32)", nx=512, ny=256, R=32.0)
+    rv, rl = WL.coexistence(wl)
+    tau = 2.0 * wl.R / wl.U
+    n_end = int(round(t_end_tau * tau))
+    every = max(1, n_end // samples)
+    layer = int(round(wl.film * wl.R + 2))
+    out = dict(workload=wl.name, tau=tau, layer=layer, every=every, t=[], r=[])
+    with lbm.Domain(WL.params(wl, precision, rv=rv, rl=rl)) as dom:
+        rho0, u0 = WL.initial_fields(wl, rv, rl)
+        dom.lbm_init_fields(rho0, u0)
+        t0 = time.perf_counter()
+        for k in range(0, n_end, every):
+            if k + every >= n_end:
+                dom.lbm_record_gamma(True)  # the last chunk's final step is recorded
+            dom.lbm_step(every)
+            out["t"].append(k + every)
+            out["r"].append(dom.lbm_crown_radius(layer))
+        out["seconds"] = time.perf_counter() - t0
+        rel = dom.lbm_read_relaxation()
+        rho, _ = dom.lbm_read_macroscopic()
+    phi = (rho - rv) / (rl - rv)
+    near1 = np.abs(rel - 1.0) < 0.05
+    iface = (phi > 0.1) & (phi < 0.9)
+    out["relaxation"] = dict(share_within_5pct=float(near1.mean()),
+                             share_within_5pct_at_interfaces=float(near1[iface].mean()) if iface.any() else None,
+                             share_within_5pct_in_bulk=float(near1[~iface].mean()))
+    hit = [i for i, r in enumerate(out["r"]) if r > 0]
+    if hit:
+        tc = out["t"][hit[0]]
+        pts = [(t - tc, r) for t, r in zip(out["t"], out["r"]) if 0.05 * tau <= t - tc <= tau and r > 0]
+        out["t_contact"] = tc
+        if len(pts) >= 3:
+            p, c = fit_power([q[0] for q in pts], [q[1] for q in pts])
+            out["fit"] = dict(p=p, c=c, points=len(pts))
+    return out
+
+
 def spurious_study(quick=False):
     """The three spurious-current sweeps and the temperature exponent."""
     if quick:
@@ -334,12 +386,12 @@ def stability_study(quick=False):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["spurious", "stability", "surface-tension"])
+    ap.add_argument("study", choices=["spurious", "stability", "surface-tension", "crown"])
     ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
     args = ap.parse_args()
     lbm.load()
     res = {"spurious": spurious_study, "stability": stability_study,
-           "surface-tension": surface_tension_study}[args.study](args.quick)
+           "surface-tension": surface_tension_study, "crown": crown_study}[args.study](args.quick)
     print(json.dumps(res), flush=True)
 
 

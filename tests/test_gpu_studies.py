@@ -62,3 +62,12 @@ def test_quick_surface_tension_sweep_gives_positive_sigma_falling_towards_tc():
     sig = {r["T_over_Tc"]: r.get("sigma") for r in res["rows"]}
     assert sig[0.6] is not None and sig[0.75] is not None
     assert sig[0.6] > sig[0.75] > 0
+
+
+def test_quick_crown_series_grows_after_contact():
+    res = S.crown_study(quick=True, t_end_tau=1.0, samples=40)
+    r = res["r"]
+    assert "t_contact" in res and r[-1] > 0
+    after = [x for x in r if x > 0]
+    assert after[-1] > after[0]  # the crown spreads
+    assert 0 <= res["relaxation"]["share_within_5pct"] <= 1
