@@ -154,6 +154,26 @@ lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count)
 lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* max_u,
                          double* gamma_field);
 
+/* A drop falling onto a liquid film (the impact of Secs. 3.2 and 3.3), built on
+ * the GPU for domains whose fields are too large to pass from the host.  With
+ * the last axis vertical (y in 2-D, z in 3-D; the film on its low face) and the
+ * drop centred at x = (nx-1)/2 [, y = (ny-1)/2], height film + radius + gap:
+ * rho = (rho_l + rho_v)/2 - (rho_l - rho_v)/2 tanh(2 d / width), d the smaller of
+ * the distance to the drop surface and the height above the film surface
+ * (film - 1/2), with rho_l, rho_v those of the domain's parameters; the velocity
+ * is -speed along the last axis times the drop's liquid fraction
+ * 1/2 - 1/2 tanh(2 d_drop / width), plus, where noise > 0, normal white noise of
+ * standard deviation noise * speed in every component, also weighted by that
+ * fraction (the perturbation of Sec. 3.3), drawn from SplitMix64 keyed by
+ * (seed, node, component).  film <= 0: no film.  Then, as lbm_init_fields, the
+ * populations start at rest in the reported sense.  LBM_ERR_INVALID_ARG for a
+ * NULL geometry or radius/width not positive.  Synchronising. */
+typedef struct {
+  double radius, film, gap, speed, width, noise;
+  uint64_t seed;
+} lbm_drop_on_film;
+lbm_status lbm_init_drop_on_film(lbm_handle h, const lbm_drop_on_film* g);
+
 /* Largest speed over the domain of the reported velocity u + F dt/(2 rho)
  * (the exact-difference-method velocity that lbm_read_macroscopic returns,
  * the velocity whose maximum the paper reports as the spurious current,

@@ -243,6 +243,10 @@ lbm_status lbm_internal_enqueue_flag_copy(lbm_domain* h, cudaStream_t stream) {
   return enqueue_flag_copy(h, stream);
 }
 
+namespace {
+lbm_status init_from_device_fields(lbm_handle h, double* buf);
+}  // namespace
+
 extern "C" {
 
 const char* lbm_version(void) { return kVersion; }
@@ -415,6 +419,30 @@ lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, co
   LBM_CUDA(h, cudaMemcpyAsync(buf + h->dev.N, ux, nb, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(h, cudaMemcpyAsync(buf + 2 * h->dev.N, uy, nb, cudaMemcpyHostToDevice, h->stream));
   if (D == 3) LBM_CUDA(h, cudaMemcpyAsync(buf + 3 * h->dev.N, uz, nb, cudaMemcpyHostToDevice, h->stream));
+  return init_from_device_fields(h, buf);
+}
+
+lbm_status lbm_init_drop_on_film(lbm_handle h, const lbm_drop_on_film* g) {
+  LBM_LIVE(h);
+  if (!g) return fail(h, LBM_ERR_INVALID_ARG, "geometry is NULL");
+  if (!(g->radius > 0) || !(g->width > 0) || !std::isfinite(g->speed) || !(g->noise >= 0) || !std::isfinite(g->film) ||
+      !std::isfinite(g->gap))
+    return fail(h, LBM_ERR_INVALID_ARG, "drop-on-film needs radius > 0, width > 0, noise >= 0 and finite film, gap, speed");
+  const int D = h->ops->D;
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)h->dev.N * sizeof(double) * (1 + D), h->stream));
+  h->ops->drop_on_film(h->dev, *g, h->p.rho_liquid, h->p.rho_vapour, buf, buf + h->dev.N, h->stream);
+  h->launches += 1;
+  return init_from_device_fields(h, buf);
+}
+
+}  // extern "C"
+
+namespace {
+// Populations at rest in the reported sense for the float64 fields in the device
+// buffer buf = [rho | ux | uy (| uz)], which this frees.
+lbm_status init_from_device_fields(lbm_handle h, double* buf) {
+  const int D = h->ops->D;
   double* uz_d = D == 3 ? buf + 3 * h->dev.N : nullptr;
   // equilibrium at the requested velocity, its auxiliary fields, then the bare velocity
   // u - F/(2 rho) and the equilibrium there, so that the reported velocity is u
@@ -430,6 +458,9 @@ lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, co
   h->steps = 0;
   return LBM_OK;
 }
+}  // namespace
+
+extern "C" {
 
 lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
   LBM_LIVE(h);

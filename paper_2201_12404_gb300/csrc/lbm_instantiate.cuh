@@ -94,6 +94,11 @@ struct Launch {
     max_speed_partial_kernel<D, S, R, A><<<blocks1d(d), 256, 0, s>>>(d, parity, partial);
     return (int)blocks1d(d);
   }
+  static void drop_on_film(const DevDomain& d, const lbm_drop_on_film& g, double rho_l, double rho_v, double* rho,
+                           double* u, cudaStream_t s) {
+    drop_on_film_kernel<D><<<blocks1d(d), 256, 0, s>>>(d, g.radius, g.film, g.gap, g.speed, g.width, g.noise,
+                                                       (unsigned long long)g.seed, rho_l, rho_v, rho, u);
+  }
   static int grad_partial(const DevDomain& d, double* partial, cudaStream_t s) {
     grad_partial_kernel<D, A><<<blocks1d(d), 256, 0, s>>>(d, partial);
     return (int)blocks1d(d);
@@ -107,7 +112,7 @@ struct Launch {
   static Ops table() {
     return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
                &canonical_read, &canonical_write, &macroscopic, &bare_velocity, &diag_partial,
-               &max_speed_partial, &grad_partial, &crown_partial};
+               &max_speed_partial, &drop_on_film, &grad_partial, &crown_partial};
   }
 };
 

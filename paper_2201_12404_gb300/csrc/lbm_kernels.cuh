@@ -239,6 +239,48 @@ __global__ void __launch_bounds__(256) max_speed_partial_kernel(DevDomain d, int
 }
 
 // ---------------------------------------------------------------------------
+// Drop-on-film initial fields (float64, natural layout): see lbm_init_drop_on_film.
+// The white noise draws from SplitMix64 (Steele, Lea & Flood 2014) keyed by
+// (seed, node, component), two uniforms per value, normal by Box-Muller.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double unit_open(unsigned long long z) {  // (0, 1]
+  return ((double)(z >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+template <int D>
+__global__ void drop_on_film_kernel(DevDomain d, double R, double film, double gap, double U, double W, double noise,
+                                    unsigned long long seed, double rho_l, double rho_v, double* rho, double* u) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.N) return;
+  const int x = (int)(n % d.nx), y = (int)((n / d.nx) % d.ny), z = (int)(n / ((long long)d.nx * d.ny));
+  const double vert = D == 3 ? (double)z : (double)y;
+  const double cv = film + R + gap;
+  const double dx = x - 0.5 * (d.nx - 1);
+  const double dy = D == 3 ? y - 0.5 * (d.ny - 1) : vert - cv;
+  const double dz = D == 3 ? vert - cv : 0.0;
+  const double d_drop = sqrt(dx * dx + dy * dy + dz * dz) - R;
+  const double d_film = film > 0 ? vert - (film - 0.5) : INFINITY;
+  const double dist = fmin(d_drop, d_film);
+  rho[n] = 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * tanh(2.0 * dist / W);
+  const double liq = 0.5 - 0.5 * tanh(2.0 * d_drop / W);
+  for (int a = 0; a < D; ++a) {
+    double v = a == D - 1 ? -U * liq : 0.0;
+    if (noise > 0) {
+      const unsigned long long key = seed ^ ((unsigned long long)n * (unsigned long long)(2 * D) + 2ull * a) * 0xD1B54A32D192ED03ull;
+      const double u1 = unit_open(splitmix64(key)), u2 = unit_open(splitmix64(key + 1));
+      v += noise * U * liq * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    }
+    u[a * d.N + n] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Largest |grad rho| of the auxiliary density (second-order central differences;
 // the ghost layer supplies the wrapped or mirrored neighbours), one partial
 // maximum per block in field 4 of the diag layout.

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -25,6 +26,9 @@ struct Ops {
   int (*diag_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
   // the same layout, field 4 = largest |u + F/(2 rho)| of the block (auxiliary fields current)
   int (*max_speed_partial)(const DevDomain&, int parity, double* partial, cudaStream_t);
+  // drop-on-film initial fields into rho[N], u[D*N] (device, float64)
+  void (*drop_on_film)(const DevDomain&, const lbm_drop_on_film& g, double rho_l, double rho_v, double* rho, double* u,
+                       cudaStream_t);
   // the same layout, field 4 = largest |grad rho| of the block (auxiliary fields current)
   int (*grad_partial)(const DevDomain&, double* partial, cudaStream_t);
   // the same layout, field 4 = crown radius of the block's nodes of one layer

@@ -85,6 +85,7 @@ def load():
                 "lbm_read_diag": (st, [H, _dp, _dp, _dp, _dp]),
                 "lbm_record_gamma": (st, [H, ctypes.c_int]),
                 "lbm_max_speed": (st, [H, _dp]),
+                "lbm_init_drop_on_film": (st, [H, ctypes.POINTER(lbm_drop_on_film)]),
                 "lbm_interface_width": (st, [H, _dp, _dp]),
                 "lbm_crown_radius": (st, [H, ctypes.c_int32, _dp]),
                 "lbm_read_relaxation": (st, [H, _dp]),
@@ -167,6 +168,12 @@ def lbm_step_noalloc(p: lbm_params, populations_ptr: int, nsteps: int) -> None:
                            "the 16 MiB scratch, or a CUDA error)")
 
 
+class lbm_drop_on_film(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_double), ("film", ctypes.c_double), ("gap", ctypes.c_double),
+                ("speed", ctypes.c_double), ("width", ctypes.c_double), ("noise", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
 class Domain:
     """One simulation domain (owns an lbm_handle)."""
 
@@ -219,6 +226,10 @@ class Domain:
         """Same call with raw host pointers (e.g. pinned torch tensors' data_ptr())."""
         c = lambda p: ctypes.cast(ctypes.c_void_p(p), _dp) if p else None
         self._c(load().lbm_init_fields(self.handle, c(rho_ptr), c(ux_ptr), c(uy_ptr), c(uz_ptr)))
+
+    def lbm_init_drop_on_film(self, radius, film, gap, speed, width, noise=0.0, seed=0):
+        g = lbm_drop_on_film(radius, film, gap, speed, width, noise, seed)
+        self._c(load().lbm_init_drop_on_film(self.handle, ctypes.byref(g)))
 
     def lbm_step(self, nsteps: int):
         self._c(load().lbm_step(self.handle, int(nsteps)))

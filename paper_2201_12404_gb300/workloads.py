@@ -35,6 +35,8 @@ class Workload:
     W: float = 5.0
     steps: int = 5000
     walls_axis: int = -1     # bounce-back on both faces of this axis, -1: fully periodic
+    a_scale: float = 1.0     # EOS constant a = a_scale * 0.003 (with kappa scaled alike W stays, sigma scales)
+    noise: float = 0.0       # white noise on the drop's velocity, std as a fraction of U (Sec. 3.3)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -72,7 +74,20 @@ DROP_IMPACT_3D_SMALL = Workload(
     D=3, nx=256, ny=256, nz=128, T_over_Tc=0.59, kappa=0.01, nu_liquid=0.005, mu_ratio=50.0,
     R=32.0, U=0.04, film=0.2, steps=5000, walls_axis=2)
 
-WORKLOADS = {"drop3d": DROP_IMPACT_3D, "drop3d-small": DROP_IMPACT_3D_SMALL, "drop2d": DROP_IMPACT_2D,
+# The paper's 3-D configuration (Sec. 3.3): R0 = 80 in a 14R0 x 14R0 x 6R0 box
+# (6.0e8 nodes, 65 GB of FP32 populations), film h = 0.44 R0 (h/2R0 = 0.22),
+# T/Tc = 0.59, nu_v = 15 nu_l, white noise of 5% of U0 on the drop's velocity.
+# U0 = 0.05 and nu_l = 0.0016 give Re = 2 U0 R0 / nu_l = 5000, within the paper's
+# 3500-6900; with the EOS and kappa of the other workloads sigma ~ 0.175 and
+# We = 2 rho_l R0 U0^2 / sigma ~ 20.  The paper's We 82-328 need sigma 4-16x
+# smaller: scaling a and kappa down together (W fixed) lowers the EOS sound speed
+# as sqrt(a), and such runs diverged at the impact at this resolution.
+DROP_IMPACT_3D_PAPER = Workload(
+    name="D3Q27 drop impact, the paper's size 1120x1120x480 (R0 = 80, h/2R0 = 0.22, Re = 5000, We ~ 20)",
+    D=3, nx=1120, ny=1120, nz=480, T_over_Tc=0.59, kappa=0.01, nu_liquid=0.0016, mu_ratio=0.0,
+    R=80.0, U=0.05, film=0.44, steps=3200, walls_axis=2, noise=0.05, extra={"nu_vapour_ratio": 15.0})
+
+WORKLOADS = {"drop3d": DROP_IMPACT_3D, "drop3d-paper": DROP_IMPACT_3D_PAPER, "drop3d-small": DROP_IMPACT_3D_SMALL, "drop2d": DROP_IMPACT_2D,
              "static2d": STATIC_DROP_2D}
 
 
@@ -80,14 +95,20 @@ def by_name(name: str) -> Workload:
     return WORKLOADS[name]
 
 
+def eos(wl: Workload):
+    return dict(PAPER_EOS, a=PAPER_EOS["a"] * wl.a_scale)
+
+
 def coexistence(wl: Workload):
     from . import lbm
-    p = lbm.lbm_default_params(T_over_Tc=wl.T_over_Tc, **PAPER_EOS)
+    p = lbm.lbm_default_params(T_over_Tc=wl.T_over_Tc, **eos(wl))
     rv, rl, _ = lbm.lbm_coexistence(p)
     return rv, rl
 
 
 def viscosities(wl: Workload, rv, rl):
+    if "nu_vapour_ratio" in wl.extra:
+        return wl.nu_liquid, wl.nu_liquid * wl.extra["nu_vapour_ratio"]
     if wl.mu_ratio <= 0:
         return wl.nu_liquid, wl.nu_liquid
     return wl.nu_liquid, wl.nu_liquid * (rl / rv) / wl.mu_ratio
@@ -105,7 +126,7 @@ def params(wl: Workload, precision, stream=None, rv=None, rl=None):
         lattice=lbm.LBM_D3Q27 if wl.D == 3 else lbm.LBM_D2Q9, precision=precision,
         nx=wl.nx, ny=wl.ny, nz=wl.nz, T_over_Tc=wl.T_over_Tc, kappa=wl.kappa,
         nu_liquid=nu_l, nu_vapour=nu_v, rho_liquid=rl, rho_vapour=rv, bc=bc,
-        stream=stream, **PAPER_EOS)
+        stream=stream, **eos(wl))
 
 
 def initial_fields(wl: Workload, rv, rl, seed=I.SEED_BASE, crop=None):
