@@ -12,7 +12,8 @@ job); e2e = the same metric through the C ABI with host buffers (initial fields
 copied in, K steps, density and velocity copied out); roofline = the
 force+collide+stream kernel's algorithmic bytes per launch over its CUDA-event
 duration, against the measured HBM copy bandwidth; cpu_baseline = the FP64
-oracle on a bounded crop of the same workload on the host cores.
+oracle on a bounded crop of the same workload on the host cores; serving (N = 1)
+= p50/p99 latency and aggregate MLUPS of a short continuous-batching run.
 
 --impl reference times the FP64 CPU oracle (the reference implementation of
 the method) on a bounded crop of the same workload; N > 1: rank 0 only.
@@ -265,6 +266,27 @@ def algorithmic_bytes_k2(wl, pop_bytes, aux_bytes):
     return wl.N * (2 * Q * pop_bytes + (2 + wl.D) * aux_bytes)
 
 
+def serving_sample(n_jobs, scale=0.05, seed=None):
+    """The served-job part of the metric: a short run of the continuous-batching
+    server (seeded Poisson arrivals at ~80% load of mixed D2Q9/D3Q27 jobs, FP32,
+    1,000-10,000 steps per job scaled by `scale`, admission by footprint against
+    half of the free HBM)."""
+    import torch
+    from paper_2201_12404_gb300 import inputs as I
+    from paper_2201_12404_gb300 import serve as SV
+    seed = I.SEED_BASE if seed is None else seed
+    jobs = SV.random_jobs(n_jobs, seed, scale)
+    total_lups = sum(j.N * j.steps for j in jobs)
+    rate = 0.8 * len(jobs) / (total_lups / 9e9)
+    free, _ = torch.cuda.mem_get_info()
+    rep = SV.serve(jobs, SV.poisson_arrivals(len(jobs), rate, seed), int(0.5 * free))
+    return {"p50_latency_s": rep["p50_latency_s"], "p99_latency_s": rep["p99_latency_s"],
+            "aggregate_mlups": rep["aggregate_mlups"], "jobs": rep["jobs"], "completed": rep["completed"],
+            "failed": rep["failed"], "admitted_while_busy": rep["admissions_while_busy"], "wall_s": rep["wall_s"],
+            "what": f"{n_jobs} seeded Poisson arrivals (rate {rate:.2f}/s), half D2Q9 64^2-1024^2, half D3Q27 "
+                    f"64^3-256^3, steps 1,000-10,000 x {scale}, FP32"}
+
+
 def algorithmic_bytes_k1(wl, pop_bytes, aux_bytes):
     """Moments+EOS kernel: each population read once; (rho, psi) and the D q planes
     written at every padded node (ghosts included)."""
@@ -388,6 +410,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and args.serve_jobs > 0:
+        line["serving"] = serving_sample(args.serve_jobs)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(wl)
     print(json.dumps(line), flush=True)
@@ -401,6 +425,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=40,
+                    help="jobs of the served-latency sample added to the line at N = 1 (0: none)")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16dev"], default="fp32",
                     help="population storage/arithmetic of the timed path (fp32 is the headline)")
     ap.add_argument("--workload", default="drop3d", choices=["drop3d", "drop3d-small", "drop2d"],
