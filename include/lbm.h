@@ -143,6 +143,18 @@ lbm_status lbm_destroy(lbm_handle h);
  * Synchronising. */
 lbm_status lbm_read_populations(lbm_handle h, double* host, size_t count);
 
+/* Canonical populations of a box of nodes, for checking or probing a part of a
+ * large domain without copying all of it.  Window node (i, j, k), 0 <= i <
+ * extent[0] and so on, is the domain node ((origin[0] + i) mod nx, (origin[1] +
+ * j) mod ny, (origin[2] + k) mod nz): a window may wrap across any face.  host
+ * receives count = Q*extent[0]*extent[1]*extent[2] float64 values in the order
+ * [i_pop][k][j][i] (x fastest), the same per-node values lbm_read_populations
+ * gives.  Needs 0 <= origin[a] < n_a and 1 <= extent[a] <= n_a on every axis
+ * (in 2-D origin[2] = 0, extent[2] = 1), else LBM_ERR_INVALID_ARG with the
+ * handle left usable.  The caller owns both arrays.  Synchronising. */
+lbm_status lbm_read_populations_window(lbm_handle h, const int64_t origin[3], const int64_t extent[3],
+                                       double* host, size_t count);
+
 /* Replace the state with canonical populations (float64, count = Q*N; rounded
  * to the storage precision).  Resets the streaming parity.  Synchronising. */
 lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count);

@@ -532,6 +532,32 @@ lbm_status lbm_read_populations(lbm_handle h, double* host, size_t count) {
   return LBM_OK;
 }
 
+lbm_status lbm_read_populations_window(lbm_handle h, const int64_t origin[3], const int64_t extent[3], double* host,
+                                       size_t count) {
+  LBM_LIVE(h);
+  if (!origin || !extent || !host) return fail(h, LBM_ERR_INVALID_ARG, "window origin, extent and buffer are required");
+  const long long n[3] = {h->dev.nx, h->dev.ny, h->dev.nz};
+  int o[3], e[3];
+  for (int a = 0; a < 3; ++a) {
+    if (origin[a] < 0 || origin[a] >= n[a] || extent[a] < 1 || extent[a] > n[a])
+      return fail(h, LBM_ERR_INVALID_ARG, "window needs 0 <= origin < n and 1 <= extent <= n on every axis");
+    o[a] = (int)origin[a];
+    e[a] = (int)extent[a];
+  }
+  const size_t m = (size_t)e[0] * e[1] * e[2];
+  const size_t want = (size_t)h->ops->Q * m;
+  if (count != want) return fail(h, LBM_ERR_INVALID_ARG, "window buffer must hold Q*ex*ey*ez doubles");
+  double* buf = nullptr;
+  LBM_CUDA(h, cudaMallocAsync(&buf, want * sizeof(double), h->stream));
+  h->ops->canonical_window(h->dev, h->parity, o, e, buf, h->stream);
+  h->launches += 1;
+  LBM_CUDA(h, cudaGetLastError());
+  LBM_CUDA(h, cudaMemcpyAsync(host, buf, want * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
 lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count) {
   LBM_LIVE(h);
   const size_t want = (size_t)h->ops->Q * h->dev.N;

@@ -76,6 +76,12 @@ struct Launch {
   static void canonical_read(const DevDomain& d, int parity, double* out, cudaStream_t s) {
     canonical_read_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, out);
   }
+  static void canonical_window(const DevDomain& d, int parity, const int o[3], const int e[3], double* out,
+                               cudaStream_t s) {
+    const long long m = (long long)e[0] * e[1] * e[2];
+    canonical_window_kernel<D, S><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d, parity, o[0], o[1], o[2], e[0], e[1],
+                                                                              e[2], out);
+  }
   static void canonical_write(const DevDomain& d, const double* in, cudaStream_t s) {
     if constexpr (DevStorage<S>::value) canonical_density_kernel<D><<<blocks1d(d), 256, 0, s>>>(d, in);
     canonical_write_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, in);
@@ -111,7 +117,7 @@ struct Launch {
   }
   static Ops table() {
     return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
-               &canonical_read, &canonical_write, &macroscopic, &bare_velocity, &diag_partial,
+               &canonical_read, &canonical_write, &canonical_window, &macroscopic, &bare_velocity, &diag_partial,
                &max_speed_partial, &drop_on_film, &grad_partial, &crown_partial};
   }
 };

@@ -118,6 +118,26 @@ __global__ void canonical_read_kernel(DevDomain d, int parity, double* out) {
   for (int i = 0; i < Q; ++i) out[(long long)i * d.N + n] = f[i];
 }
 
+// The same for the nodes of a box: window node (i, j, k) is domain node
+// ((ox + i) mod nx, (oy + j) mod ny, (oz + k) mod nz); the host checks 0 <= o < n
+// and 1 <= e <= n per axis, so o + i < 2n never overflows.
+template <int D, typename S>
+__global__ void canonical_window_kernel(DevDomain d, int parity, int ox, int oy, int oz, int ex, int ey, int ez,
+                                        double* out) {
+  constexpr int Q = Lattice<D>::Q;
+  const long long m = (long long)ex * ey * ez;
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const int i = (int)(k % ex), j = (int)((k / ex) % ey), l = (int)(k / ((long long)ex * ey));
+  int x = ox + i, y = oy + j, z = oz + l;
+  if (x >= d.nx) x -= d.nx;
+  if (y >= d.ny) y -= d.ny;
+  if (z >= d.nz) z -= d.nz;
+  double f[Q];
+  gather<D, S, double>(d, parity, x, y, z, f);
+  for (int q = 0; q < Q; ++q) out[(long long)q * m + k] = f[q];
+}
+
 template <int D, typename S>
 __global__ void canonical_write_kernel(DevDomain d, const double* in) {
   constexpr int Q = Lattice<D>::Q;

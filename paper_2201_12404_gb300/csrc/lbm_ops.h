@@ -19,6 +19,10 @@ struct Ops {
                            const double* uz, cudaStream_t);
   void (*canonical_read)(const DevDomain&, int parity, double* out, cudaStream_t);
   void (*canonical_write)(const DevDomain&, const double* in, cudaStream_t);
+  // canonical populations of the box origin + [0, extent) (coordinates wrapped
+  // modulo the domain) into out[Q][ez][ey][ex]
+  void (*canonical_window)(const DevDomain&, int parity, const int origin[3], const int extent[3], double* out,
+                           cudaStream_t);
   void (*macroscopic)(const DevDomain&, int parity, double* rho, double* u, cudaStream_t);
   // u[a*N + n] -= F_a/(2 rho[n]), F from the current auxiliary fields
   void (*bare_velocity)(const DevDomain&, const double* rho, double* u, cudaStream_t);

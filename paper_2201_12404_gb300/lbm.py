@@ -82,6 +82,8 @@ def load():
                 "lbm_destroy": (st, [H]),
                 "lbm_read_populations": (st, [H, _dp, ctypes.c_size_t]),
                 "lbm_write_populations": (st, [H, _dp, ctypes.c_size_t]),
+                "lbm_read_populations_window": (st, [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                                     _dp, ctypes.c_size_t]),
                 "lbm_read_diag": (st, [H, _dp, _dp, _dp, _dp]),
                 "lbm_record_gamma": (st, [H, ctypes.c_int]),
                 "lbm_max_speed": (st, [H, _dp]),
@@ -252,6 +254,15 @@ class Domain:
         out = np.empty(self.Q * self.N)
         self._c(load().lbm_read_populations(self.handle, _ptr(out), out.size))
         return out.reshape((self.Q,) + self.shape)
+
+    def lbm_read_populations_window(self, origin, extent):
+        """Populations of the box origin + [0, extent) (x, y, z order; wraps across
+        faces) as an array (Q, ez, ey, ex)."""
+        o = (ctypes.c_int64 * 3)(*[int(v) for v in (tuple(origin) + (0, 0, 0))[:3]])
+        e = (ctypes.c_int64 * 3)(*[int(v) for v in (tuple(extent) + (1, 1, 1))[:3]])
+        out = np.empty(self.Q * e[0] * e[1] * e[2])
+        self._c(load().lbm_read_populations_window(self.handle, o, e, _ptr(out), out.size))
+        return out.reshape((self.Q, e[2], e[1], e[0]))
 
     def lbm_write_populations(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)

@@ -1,0 +1,100 @@
+"""GPU parity at the benchmark's full sizes, on sampled windows.
+
+The benchmark domains (D3Q27 512x512x256 and D2Q9 2048x1024 drop impacts, walls
+on the vertical axis, periodic elsewhere) are stepped on the GPU exactly as the
+benchmark steps them: the same parameters, the same seeded initial fields through
+lbm_init_fields, the same grid and kernels, on a dedicated stream.  The oracle
+cannot step 67M nodes in a test, but one node after K steps depends only on the
+initial fields within a radius of 3K + 2 (Sec. 2: the force reaches two nodes,
+streaming one more; the initial velocity shift F/(2 rho) reaches two).  So for
+each sample node the oracle runs K steps on a window of the initial fields with
+that margin around the nodes it checks, and those nodes are compared with the
+GPU's state read back through lbm_read_populations_window.
+
+Windows wrap across the periodic faces like the domain does; along the wall axis
+a window is clipped to the domain, and a face that is not a true wall gets a
+bounce-back wall in the oracle, whose effect stays inside the margin.
+
+Tolerances (per population, relative to w_i rho):
+ - FP64: 1e-12 per step plus the initial state, as for the small parity cases;
+ - FP32: 2e-6 per step plus the initial state (the initial equilibria are
+   rounded to float32 on the GPU);
+ - FP16 deviations: 1e-3 per stored state (the bound of one half-precision
+   store of a deviation at writer/reader density ratios up to ~3).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from cases import rel_err
+from windows import K, oracle_window, sample_nodes, window_axis
+from oracle import thermo
+from paper_2201_12404_gb300 import lbm
+from paper_2201_12404_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lbm.LBM_FP64: 1e-12, lbm.LBM_FP32: 2e-6, lbm.LBM_FP16DEV: 1e-3}
+
+
+@pytest.fixture(scope="module", params=["drop3d", "drop2d"])
+def workload(request):
+    wl = WL.by_name(request.param)
+    rv, rl, _ = thermo.maxwell(wl.T_over_Tc, **WL.eos(wl))
+    rho0, u0 = WL.initial_fields(wl, rv, rl)
+    return wl, rv, rl, rho0, u0
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_FP32, lbm.LBM_FP64, lbm.LBM_FP16DEV], ids=["fp32", "fp64", "fp16dev"])
+def test_full_size_samples_match_oracle(workload, precision):
+    torch = pytest.importorskip("torch")
+    wl, rv, rl, rho0, u0 = workload
+    if wl.D == 2 and precision == lbm.LBM_FP16DEV:
+        pytest.skip("the float16-deviation benchmark line is the 3-D workload")
+    stream = torch.cuda.Stream()
+    p = WL.params(wl, precision, stream=stream.cuda_stream, rv=rv, rl=rl)
+    walls = [wl.walls_axis == a for a in range(wl.D)]
+    n = (wl.nx, wl.ny, wl.nz)[:wl.D]
+    worst, nodes = 0.0, 0
+    with lbm.Domain(p) as dom:
+        dom.lbm_init_fields(rho0, u0)
+        dom.lbm_step(K)
+        dom.lbm_synchronize()
+        for s in sample_nodes(wl):
+            axes = [window_axis(c, m, w) for c, m, w in zip(s, n, walls)]
+            for (lo, length, _, valid), c, m in zip(axes, s, n):
+                assert valid.start <= (c - lo) % m < valid.stop  # the sample is among the checked nodes
+            fg = dom.lbm_read_populations_window([a[0] for a in axes], [a[1] for a in axes])
+            po, f0 = oracle_window(wl, rv, rl, rho0, u0, axes)
+            if precision == lbm.LBM_FP32:
+                f0 = f0.astype(np.float32).astype(np.float64)
+            fo, _ = O.run(po, f0, K)
+            sel = (slice(None),) + tuple(a[3] for a in reversed(axes)) if wl.D == 3 else \
+                (slice(None), slice(None)) + tuple(a[3] for a in reversed(axes))
+            e = rel_err(fg[sel], fo[sel], wl.D).max()
+            assert e <= (K + 1) * TOL[precision], (s, e)
+            worst, nodes = max(worst, e), nodes + fg[sel][0].size
+    print(f"\n{wl.nx}x{wl.ny}x{wl.nz} precision {precision}: largest error {worst:.3e} over {nodes} sampled nodes")
+
+
+def test_window_read_matches_full_read_and_rejects_bad_boxes():
+    """A wrapped window equals the same nodes of lbm_read_populations, at both
+    streaming parities; out-of-range boxes are refused with the handle usable."""
+    from cases import case, drop_state, lbm_params
+    c = case(3, 21, 10, 9, walls=True, precision=lbm.LBM_FP32)
+    f0 = drop_state(c).astype(np.float32).astype(np.float64)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(f0)
+        for steps in (0, 1):
+            dom.lbm_step(steps)
+            full = dom.lbm_read_populations()
+            win = dom.lbm_read_populations_window((17, 7, 3), (9, 6, 9))
+            iz, iy, ix = (3 + np.arange(9)) % 9, (7 + np.arange(6)) % 10, (17 + np.arange(9)) % 21
+            assert np.array_equal(win, full[(slice(None),) + np.ix_(iz, iy, ix)])
+        for origin, extent in (((21, 0, 0), (1, 1, 1)), ((0, 0, 0), (22, 1, 1)), ((0, 0, 0), (0, 1, 1)),
+                               ((-1, 0, 0), (1, 1, 1))):
+            with pytest.raises(lbm.LBMError) as e:
+                dom.lbm_read_populations_window(origin, extent)
+            assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+        dom.lbm_step(1)  # still usable
+        dom.lbm_synchronize()
