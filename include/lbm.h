@@ -107,8 +107,10 @@ typedef struct {
 lbm_status lbm_default_params(lbm_params* p);
 
 /* Validate p, allocate the domain's device memory and create its handle.
- * *out receives the handle (NULL on failure).  Errors: INVALID_ARG (message via
- * lbm_last_error(NULL)), OOM, CUDA. */
+ * *out receives the handle (NULL on failure).  Errors (message via
+ * lbm_last_error(NULL)): INVALID_ARG; OOM when lbm_footprint_bytes(p) exceeds
+ * the device's free memory (checked before anything is allocated) or an
+ * allocation fails; CUDA. */
 lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out);
 
 /* Initial state from host arrays of N values each (uz is NULL in 2-D): the

@@ -332,6 +332,18 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
   *out = nullptr;
   const std::string why = validate(p);
   if (!why.empty()) { g_create_error = why; return LBM_ERR_INVALID_ARG; }
+  {
+    // refuse a domain that cannot fit before allocating any of it
+    size_t free_b = 0, total_b = 0;
+    const cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) { g_create_error = std::string("cudaMemGetInfo: ") + cudaGetErrorString(e); return LBM_ERR_CUDA; }
+    const size_t need = lbm_footprint_bytes(p);
+    if (need > free_b) {
+      g_create_error = "domain needs " + std::to_string(need) + " bytes of device memory, " + std::to_string(free_b) +
+                       " are free";
+      return LBM_ERR_OOM;
+    }
+  }
 
   lbm_domain* h = new lbm_domain();
   h->p = *p;

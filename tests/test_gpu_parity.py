@@ -120,6 +120,21 @@ def test_minimum_size_domain():
     assert rel_err(fg, fo, 2).max() <= 2e-12
 
 
+def test_domain_larger_than_free_memory_is_refused_before_allocating():
+    """A D3Q27 FP64 domain of 2.25e9 nodes needs ~490 GB: refused with LBM_ERR_OOM
+    from the free-memory check, and the device stays usable."""
+    p = lbm.lbm_default_params(lattice=lbm.LBM_D3Q27, precision=lbm.LBM_FP64, nx=1500, ny=1500, nz=1000)
+    assert lbm.lbm_footprint_bytes(p) > 400e9
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Domain(p)
+    assert e.value.status == lbm.LBM_ERR_OOM and "free" in str(e.value)
+    c = case(2, 16, 16)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_write_populations(drop_state(c))
+        dom.lbm_step(2)
+        dom.lbm_synchronize()
+
+
 def test_macroscopic_matches_oracle():
     for D, dims in ((2, dict(nx=40, ny=30)), (3, dict(nx=17, ny=12, nz=10))):
         c = case(D, **dims)
