@@ -12,7 +12,9 @@
  * with the product-form equilibria of Sec. 2.2 (Eqs. LBMeq, LBMstar), the
  * Peng-Robinson pressure of Sec. 3.1 (Eq. PREoS) entering through the
  * pseudo-potential force of Sec. 2.3 (Eq. Kforce_final), the diagonal
- * correction Phi (Eq. correction), and the entropic mirror state of Sec. 2.4
+ * correction Phi (Eq. correction, with the sign that cancels the lattice's
+ * third-moment defect, the job Sec. 2.2 gives it; the printed sign doubles the
+ * defect), and the entropic mirror state of Sec. 2.4
  * (k/s/h split in the central Hermite basis of Appendix A, gamma from the
  * entropic scalar products).
  *

@@ -78,47 +78,52 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def load_library(path: str):
+    """Open a compiled oracle library and declare its C signatures."""
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER(Params)
+    sig = {
+        "orc_Q": (ctypes.c_int, [ctypes.c_int]),
+        "orc_velocities": (None, [ctypes.c_int, _ip]),
+        "orc_psi1": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+        "orc_product_form": (None, [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]),
+        "orc_weights": (None, [ctypes.c_int, _dp]),
+        "orc_feq": (None, [ctypes.c_int, ctypes.c_double, _dp, _dp]),
+        "orc_fstar": (None, [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]),
+        "orc_Tc": (ctypes.c_double, [P]),
+        "orc_pressure": (ctypes.c_double, [P, ctypes.c_double]),
+        "orc_psi": (ctypes.c_double, [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+        "orc_omega": (ctypes.c_double, [P, ctypes.c_double]),
+        "orc_central_moments": (None, [ctypes.c_int, _dp, _dp, _dp]),
+        "orc_basis_rows": (None, [ctypes.c_int, _ip, _ip, _ip]),
+        "orc_kbc_split": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
+        "orc_collide_node": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double,
+                                            ctypes.c_int, ctypes.c_double, _dp,
+                                            ctypes.POINTER(ctypes.c_double),
+                                            _dp, _dp, _dp, _dp, _dp]),
+        "orc_aux_fields": (None, [P, _dp, _dp, _dp, _dp, _dp]),
+        "orc_force": (None, [P, _dp, _dp, _dp]),
+        "orc_phi": (None, [P, _dp, _dp, _dp]),
+        "orc_init_equilibrium": (None, [P, _dp, _dp, _dp]),
+        "orc_init_physical": (None, [P, _dp, _dp, _dp]),
+        "orc_macroscopic": (None, [P, _dp, _dp, _dp]),
+        "orc_step": (ctypes.c_long, [P, _dp, _dp, ctypes.c_void_p]),
+        "orc_run": (ctypes.c_long, [P, _dp, ctypes.c_long]),
+        "orc_totals": (None, [P, _dp, ctypes.POINTER(ctypes.c_double), _dp]),
+        "orc_num_threads": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            P = ctypes.POINTER(Params)
-            sig = {
-                "orc_Q": (ctypes.c_int, [ctypes.c_int]),
-                "orc_velocities": (None, [ctypes.c_int, _ip]),
-                "orc_psi1": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double]),
-                "orc_product_form": (None, [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]),
-                "orc_weights": (None, [ctypes.c_int, _dp]),
-                "orc_feq": (None, [ctypes.c_int, ctypes.c_double, _dp, _dp]),
-                "orc_fstar": (None, [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]),
-                "orc_Tc": (ctypes.c_double, [P]),
-                "orc_pressure": (ctypes.c_double, [P, ctypes.c_double]),
-                "orc_psi": (ctypes.c_double, [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
-                "orc_omega": (ctypes.c_double, [P, ctypes.c_double]),
-                "orc_central_moments": (None, [ctypes.c_int, _dp, _dp, _dp]),
-                "orc_basis_rows": (None, [ctypes.c_int, _ip, _ip, _ip]),
-                "orc_kbc_split": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]),
-                "orc_collide_node": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double,
-                                                    ctypes.c_int, ctypes.c_double, _dp,
-                                                    ctypes.POINTER(ctypes.c_double),
-                                                    _dp, _dp, _dp, _dp, _dp]),
-                "orc_aux_fields": (None, [P, _dp, _dp, _dp, _dp, _dp]),
-                "orc_force": (None, [P, _dp, _dp, _dp]),
-                "orc_phi": (None, [P, _dp, _dp, _dp]),
-                "orc_init_equilibrium": (None, [P, _dp, _dp, _dp]),
-                "orc_init_physical": (None, [P, _dp, _dp, _dp]),
-                "orc_macroscopic": (None, [P, _dp, _dp, _dp]),
-                "orc_step": (ctypes.c_long, [P, _dp, _dp, ctypes.c_void_p]),
-                "orc_run": (ctypes.c_long, [P, _dp, ctypes.c_long]),
-                "orc_totals": (None, [P, _dp, ctypes.POINTER(ctypes.c_double), _dp]),
-                "orc_num_threads": (ctypes.c_int, []),
-            }
-            for name, (res, args) in sig.items():
-                fn = getattr(L, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = L
+            _lib = load_library(build())
     return _lib
 
 

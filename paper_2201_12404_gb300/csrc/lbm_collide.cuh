@@ -7,7 +7,8 @@
 //   - gathers its Q pre-collision populations (A-A parity aware) into registers,
 //   - forms rho, j, Pi from row sums (the three populations sharing (cy, cz)),
 //   - evaluates the force of Eq. (Kforce_final) with the physical sign from the
-//     staged tile, and Phi of Eq. (correction) from q = rho u^3,
+//     staged tile, and Phi of Eq. (correction) from q = rho u^3 (with the sign
+//     that cancels the lattice's third-moment defect),
 //   - builds the one-dimensional factors of f^eq (Eq. LBMeq), f* (Eq. LBMstar)
 //     and of the dual basis of the central Hermite moments (Appendix A),
 //   - pass A: h = f - f^eq - s per population, the entropic sums
@@ -380,7 +381,10 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     F[2] = D == 3 ? rho * ph.g[2] - (tz.x + tz.y) : (R)0;
   }
 
-  // ---- Phi_aa = (1 - omega/2) d_a q_a, central difference
+  // ---- Phi_aa = -(1 - omega/2) d_a q_a, central difference.  The sign is the one
+  // that cancels the lattice's third-moment defect (sum f^eq c_a^3 = rho u_a where
+  // rho u_a^3 + 3 P0 u_a is due) in the diagonal momentum flux, the purpose Sec. 2.2
+  // gives Phi; Eq. (correction) prints the opposite sign, which doubles the defect.
   const R om = omega_of<R>(ph, rho);
   R Phi[3] = {0, 0, 0};
   if (kTma) {
@@ -390,7 +394,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     for (int a = 0; a < D; ++a) {
       const A* qa = s_q + a * H::template qstride<A>() + qc;
       const int e = a == 0 ? 1 : (a == 1 ? H::QX : H::QX * H::QY);
-      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[e] - (R)qa[-e]) * (R)0.5;
+      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[-e] - (R)qa[e]) * (R)0.5;
     }
   } else {
     const A* a_q = (const A*)d.aux + 2 * d.PN;
@@ -400,7 +404,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     for (int a = 0; a < D; ++a) {
       const A* qa = a_q + a * d.PN;
       const long long e = a == 0 ? 1 : (a == 1 ? sy : sz);
-      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc + e] - (R)qa[pc - e]) * (R)0.5;
+      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc - e] - (R)qa[pc + e]) * (R)0.5;
     }
   }
   if (kStaged) {
