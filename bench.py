@@ -348,6 +348,12 @@ def run_ours(args):
     h_rho, h_u = pin(rho0), [pin(u0[k]) for k in range(wl.D)]
     o_rho = torch.empty(wl.N, dtype=torch.float64).pin_memory()
     o_u = [torch.empty(wl.N, dtype=torch.float64).pin_memory() for _ in range(wl.D)]
+    # one untimed pass through the same two calls, so that the timed pass does not pay
+    # for first use of the library's device memory pool
+    dom.lbm_init_fields_ptr(h_rho.data_ptr(), h_u[0].data_ptr(), h_u[1].data_ptr(),
+                            h_u[2].data_ptr() if wl.D == 3 else None)
+    dom.lbm_read_macroscopic_ptr(o_rho.data_ptr(), o_u[0].data_ptr(), o_u[1].data_ptr(),
+                                 o_u[2].data_ptr() if wl.D == 3 else None)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -456,14 +456,13 @@ namespace {
 lbm_status init_from_device_fields(lbm_handle h, double* buf) {
   const int D = h->ops->D;
   double* uz_d = D == 3 ? buf + 3 * h->dev.N : nullptr;
-  // equilibrium at the requested velocity, its auxiliary fields, then the bare velocity
-  // u - F/(2 rho) and the equilibrium there, so that the reported velocity is u
-  h->ops->init_equilibrium(h->dev, buf, buf + h->dev.N, buf + 2 * h->dev.N, uz_d, h->stream);
+  // the (rho, psi) pairs of the density field, the force they give, the bare velocity
+  // u - F/(2 rho), and the equilibrium there, so that the reported velocity is u
+  h->ops->aux_density(h->dev, buf, h->stream);
   h->parity = 0;
-  h->ops->moments_eos(h->dev, 0, h->stream);
   h->ops->bare_velocity(h->dev, buf, buf + h->dev.N, h->stream);
   h->ops->init_equilibrium(h->dev, buf, buf + h->dev.N, buf + 2 * h->dev.N, uz_d, h->stream);
-  h->launches += 4;
+  h->launches += 3;
   LBM_CUDA(h, cudaGetLastError());
   LBM_CUDA(h, cudaFreeAsync(buf, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -71,7 +71,12 @@ struct Launch {
   static unsigned blocks1d(const DevDomain& d) { return (unsigned)((d.N + 255) / 256); }
   static void init_equilibrium(const DevDomain& d, const double* rho, const double* ux, const double* uy,
                                const double* uz, cudaStream_t s) {
-    init_equilibrium_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, rho, ux, uy, uz);
+    init_equilibrium_kernel<D, S, R><<<blocks1d(d), 256, 0, s>>>(d, rho, ux, uy, uz);
+  }
+  static void aux_density(const DevDomain& d, const double* rho, cudaStream_t s) {
+    dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
+    dim3 grd((d.px + blk.x - 1) / blk.x, (d.py + blk.y - 1) / blk.y, (d.pz + blk.z - 1) / blk.z);
+    aux_density_kernel<D, R, A><<<grd, blk, 0, s>>>(d, rho);
   }
   static void canonical_read(const DevDomain& d, int parity, double* out, cudaStream_t s) {
     canonical_read_kernel<D, S><<<blocks1d(d), 256, 0, s>>>(d, parity, out);
@@ -116,7 +121,7 @@ struct Launch {
     return (int)nb;
   }
   static Ops table() {
-    return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium,
+    return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium, &aux_density,
                &canonical_read, &canonical_write, &canonical_window, &macroscopic, &bare_velocity, &diag_partial,
                &max_speed_partial, &drop_on_film, &grad_partial, &crown_partial};
   }

@@ -19,20 +19,24 @@ namespace lbm {
 // interior node it images (periodic wrap or mirror across a half-way wall);
 // q is negated across a wall (no-slip image).
 // ---------------------------------------------------------------------------
+// Interior coordinate that padded coordinate cp (ghost layers of 2) images along
+// an axis of n nodes: periodic wrap, or the mirror across a half-way wall (which
+// sets *flip).
+__device__ __forceinline__ int ghost_image(int cp, int n, int wlo, int whi, bool* flip) {
+  int t = cp - 2;
+  if (t < 0) { if (wlo) { t = -1 - t; *flip = true; } else t += n; }
+  else if (t >= n) { if (whi) { t = 2 * n - 1 - t; *flip = true; } else t -= n; }
+  return t;
+}
+
 template <int D, int P, typename S, typename R, typename A>
 __device__ __forceinline__ void moments_eos_node(const DevDomain& d, int xp, int yp, int zp) {
   constexpr int Q = Lattice<D>::Q;
   if (xp >= d.nx + 4 || yp >= d.py || zp >= d.pz) return;
   bool flip = false;
-  auto image = [&](int c, int n, int wlo, int whi) {
-    int t = c - 2;
-    if (t < 0) { if (wlo) { t = -1 - t; flip = true; } else t += n; }
-    else if (t >= n) { if (whi) { t = 2 * n - 1 - t; flip = true; } else t -= n; }
-    return t;
-  };
-  const int x = image(xp, d.nx, d.wall_lo[0], d.wall_hi[0]);
-  const int y = image(yp, d.ny, d.wall_lo[1], d.wall_hi[1]);
-  const int z = D == 3 ? image(zp, d.nz, d.wall_lo[2], d.wall_hi[2]) : 0;
+  const int x = ghost_image(xp, d.nx, d.wall_lo[0], d.wall_hi[0], &flip);
+  const int y = ghost_image(yp, d.ny, d.wall_lo[1], d.wall_hi[1], &flip);
+  const int z = D == 3 ? ghost_image(zp, d.nz, d.wall_lo[2], d.wall_hi[2], &flip) : 0;
 
   R f[Q];
   gather<D, P, S, R>(d, x, y, z, f);
@@ -53,6 +57,25 @@ __device__ __forceinline__ void moments_eos_node(const DevDomain& d, int xp, int
   }
 }
 
+// The (rho, psi) pairs of every padded node straight from a density field
+// (device, float64, N values), ghosts included: what pass 1 writes for a state
+// whose density is that field, without forming populations first.  q is left
+// alone (the next pass 1 writes it).
+template <int D, typename R, typename A>
+__global__ void __launch_bounds__(256) aux_density_kernel(DevDomain d, const double* rho_in) {
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x, yp = blockIdx.y * blockDim.y + threadIdx.y;
+  const int zp = blockIdx.z * blockDim.z + threadIdx.z;
+  if (xp >= d.nx + 4 || yp >= d.py || zp >= d.pz) return;
+  bool flip = false;
+  const int x = ghost_image(xp, d.nx, d.wall_lo[0], d.wall_hi[0], &flip);
+  const int y = ghost_image(yp, d.ny, d.wall_lo[1], d.wall_hi[1], &flip);
+  const int z = D == 3 ? ghost_image(zp, d.nz, d.wall_lo[2], d.wall_hi[2], &flip) : 0;
+  const R rho = (R)rho_in[node_of(d, x, y, z)];
+  if (!(rho > (R)0) || !(rho < (R)INFINITY)) atomicOr(d.flags, 1u);
+  const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * (long long)zp);
+  ((Two<A>*)d.aux)[pn] = two<A>((A)rho, (A)psi_of<R>(d, rho));
+}
+
 template <int D, int P, typename S, typename R, typename A>
 __global__ void __launch_bounds__(256) moments_eos_kernel(DevDomain d) {
   moments_eos_node<D, P, S, R, A>(d, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
@@ -68,20 +91,20 @@ namespace lbm {
 // ---------------------------------------------------------------------------
 // f := f^eq(rho, u) at every node (natural layout, parity 0).
 // ---------------------------------------------------------------------------
-template <int D, typename S>
+template <int D, typename S, typename R>
 __global__ void init_equilibrium_kernel(DevDomain d, const double* rho, const double* ux,
                                         const double* uy, const double* uz) {
   constexpr int Q = Lattice<D>::Q;
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.N) return;
-  const double r = rho[n];
-  const double u[3] = {ux[n], uy[n], D == 3 ? uz[n] : 0.0};
-  double X[3][3];
+  const R r = (R)rho[n];
+  const R u[3] = {(R)ux[n], (R)uy[n], D == 3 ? (R)uz[n] : (R)0};
+  R X[3][3];
   for (int a = 0; a < 3; ++a) {
-    const double u2 = u[a] * u[a];
-    X[a][1] = a < D ? 1.0 - 1.0 / 3.0 - u2 : 1.0;
-    X[a][2] = a < D ? 0.5 * (1.0 / 3.0 + u2 + u[a]) : 0.0;
-    X[a][0] = a < D ? 0.5 * (1.0 / 3.0 + u2 - u[a]) : 0.0;
+    const R u2 = u[a] * u[a];
+    X[a][1] = a < D ? (R)1 - (R)(1.0 / 3.0) - u2 : (R)1;
+    X[a][2] = a < D ? (R)0.5 * ((R)(1.0 / 3.0) + u2 + u[a]) : (R)0;
+    X[a][0] = a < D ? (R)0.5 * ((R)(1.0 / 3.0) + u2 - u[a]) : (R)0;
   }
   S* F = (S*)d.f;
   if constexpr (DevStorage<S>::value) {
@@ -93,14 +116,14 @@ __global__ void init_equilibrium_kernel(DevDomain d, const double* rho, const do
     d.rho_w[0][n] = (float)r;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double rw = (double)(float)rho[upstream_node<D>(d, fast, xb, x, y, z, n, i)];
-      const double feq = r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1];
-      F[(long long)i * d.N + n] = __float2half_rn((float)(feq / (wq<D>(i) * rw) - 1.0));
+      const R rw = (R)(float)rho[upstream_node<D>(d, fast, xb, x, y, z, n, i)];
+      const R feq = r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1];
+      F[(long long)i * d.N + n] = __float2half_rn((float)(feq / ((R)wq<D>(i) * rw) - (R)1));
     }
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      st_pop<S, double>(F + (long long)i * d.N + n, r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1]);
+      st_pop<S, R>(F + (long long)i * d.N + n, r * X[0][cxi(i) + 1] * X[1][cyi(i) + 1] * X[2][D == 3 ? czi(i) + 1 : 1]);
   }
 }
 

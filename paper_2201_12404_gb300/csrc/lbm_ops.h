@@ -17,6 +17,8 @@ struct Ops {
   void (*collide_stream)(const DevDomain&, const TileMaps& maps, int parity, cudaStream_t);
   void (*init_equilibrium)(const DevDomain&, const double* rho, const double* ux, const double* uy,
                            const double* uz, cudaStream_t);
+  // (rho, psi) pairs of every padded node from a density field (device, float64)
+  void (*aux_density)(const DevDomain&, const double* rho, cudaStream_t);
   void (*canonical_read)(const DevDomain&, int parity, double* out, cudaStream_t);
   void (*canonical_write)(const DevDomain&, const double* in, cudaStream_t);
   // canonical populations of the box origin + [0, extent) (coordinates wrapped
