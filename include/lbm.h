@@ -27,7 +27,9 @@
  *    9(cz+1), holding the post-streaming, pre-collision state.  The opposite
  *    direction of i is Q-1-i.
  *  - The library owns all device memory of a domain (allocated in
- *    lbm_create_domain, freed in lbm_destroy).
+ *    lbm_create_domain, freed in lbm_destroy).  Calls that take host buffers
+ *    stage them in scratch device memory from a pool of the library's own,
+ *    which keeps up to 4 GiB per device between calls.
  *  - Every call that launches GPU work enqueues it on the domain's stream and
  *    returns without waiting, except those documented as synchronising.
  *  - Handles are not thread-safe: use one handle per host thread or lock.

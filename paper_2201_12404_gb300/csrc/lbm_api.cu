@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -100,6 +101,40 @@ lbm_status cuda_fail(lbm_domain* h, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
   } while (0)
+
+// Scratch buffers of the host-buffer calls come from a pool of the library's own
+// that keeps up to kScratchKeep bytes across synchronisations.  The default pool
+// hands its memory back at every synchronisation, and mapping a few GB again on
+// the next call costs up to a fifth of a second.
+constexpr uint64_t kScratchKeep = 4ull << 30;
+
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = kScratchKeep;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
+// Stream-ordered scratch allocation on h's stream (freed with cudaFreeAsync).
+template <typename T>
+cudaError_t scratch_alloc(lbm_domain* h, T** p, size_t bytes) {
+  cudaMemPool_t pool = scratch_pool();
+  if (!pool) return cudaMallocAsync((void**)p, bytes, h->stream);
+  return cudaMallocFromPoolAsync((void**)p, bytes, pool, h->stream);
+}
 
 #define LBM_LIVE(h)                                                               \
   do {                                                                            \
@@ -223,7 +258,7 @@ lbm_status reduce_max(lbm_handle h, Partial partial, double* out) {
   if (st != LBM_OK) return st;
   const long long nblk = (h->dev.N + 255) / 256;
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)(nblk * 5 + 5) * sizeof(double), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, (size_t)(nblk * 5 + 5) * sizeof(double)));
   const int nb = partial(buf);
   lbm::launch_diag_final(buf, nb, buf + nblk * 5, h->stream);
   h->launches += 2;
@@ -426,7 +461,7 @@ lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, co
   if (!rho || !ux || !uy || (D == 3 && !uz)) return fail(h, LBM_ERR_INVALID_ARG, "NULL field array");
   const size_t nb = (size_t)h->dev.N * sizeof(double);
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, nb * (1 + D), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, nb * (1 + D)));
   LBM_CUDA(h, cudaMemcpyAsync(buf, rho, nb, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(h, cudaMemcpyAsync(buf + h->dev.N, ux, nb, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(h, cudaMemcpyAsync(buf + 2 * h->dev.N, uy, nb, cudaMemcpyHostToDevice, h->stream));
@@ -442,7 +477,7 @@ lbm_status lbm_init_drop_on_film(lbm_handle h, const lbm_drop_on_film* g) {
     return fail(h, LBM_ERR_INVALID_ARG, "drop-on-film needs radius > 0, width > 0, noise >= 0 and finite film, gap, speed");
   const int D = h->ops->D;
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)h->dev.N * sizeof(double) * (1 + D), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, (size_t)h->dev.N * sizeof(double) * (1 + D)));
   h->ops->drop_on_film(h->dev, *g, h->p.rho_liquid, h->p.rho_vapour, buf, buf + h->dev.N, h->stream);
   h->launches += 1;
   return init_from_device_fields(h, buf);
@@ -516,7 +551,7 @@ lbm_status lbm_read_macroscopic(lbm_handle h, double* rho, double* ux, double* u
   if (st != LBM_OK) return st;
   const size_t nb = (size_t)h->dev.N * sizeof(double);
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, nb * (1 + D), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, nb * (1 + D)));
   h->ops->macroscopic(h->dev, h->parity, buf, buf + h->dev.N, h->stream);
   h->launches += 1;
   LBM_CUDA(h, cudaGetLastError());
@@ -533,7 +568,7 @@ lbm_status lbm_read_populations(lbm_handle h, double* host, size_t count) {
   const size_t want = (size_t)h->ops->Q * h->dev.N;
   if (!host || count != want) return fail(h, LBM_ERR_INVALID_ARG, "populations buffer must hold Q*N doubles");
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, want * sizeof(double), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, want * sizeof(double)));
   h->ops->canonical_read(h->dev, h->parity, buf, h->stream);
   h->launches += 1;
   LBM_CUDA(h, cudaGetLastError());
@@ -559,7 +594,7 @@ lbm_status lbm_read_populations_window(lbm_handle h, const int64_t origin[3], co
   const size_t want = (size_t)h->ops->Q * m;
   if (count != want) return fail(h, LBM_ERR_INVALID_ARG, "window buffer must hold Q*ex*ey*ez doubles");
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, want * sizeof(double), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, want * sizeof(double)));
   h->ops->canonical_window(h->dev, h->parity, o, e, buf, h->stream);
   h->launches += 1;
   LBM_CUDA(h, cudaGetLastError());
@@ -574,7 +609,7 @@ lbm_status lbm_write_populations(lbm_handle h, const double* host, size_t count)
   const size_t want = (size_t)h->ops->Q * h->dev.N;
   if (!host || count != want) return fail(h, LBM_ERR_INVALID_ARG, "populations buffer must hold Q*N doubles");
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, want * sizeof(double), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, want * sizeof(double)));
   LBM_CUDA(h, cudaMemcpyAsync(buf, host, want * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   h->ops->canonical_write(h->dev, buf, h->stream);
   h->launches += 1;
@@ -589,7 +624,7 @@ lbm_status lbm_read_diag(lbm_handle h, double* mass, double* momentum3, double* 
   LBM_LIVE(h);
   const long long nblk = (h->dev.N + 255) / 256;
   double* buf = nullptr;
-  LBM_CUDA(h, cudaMallocAsync(&buf, (size_t)(nblk * 5 + 5) * sizeof(double), h->stream));
+  LBM_CUDA(h, scratch_alloc(h, &buf, (size_t)(nblk * 5 + 5) * sizeof(double)));
   int nb = h->ops->diag_partial(h->dev, h->parity, buf, h->stream);
   lbm::launch_diag_final(buf, nb, buf + nblk * 5, h->stream);
   h->launches += 2;
