@@ -135,6 +135,31 @@ def test_domain_larger_than_free_memory_is_refused_before_allocating():
         dom.lbm_synchronize()
 
 
+def test_host_buffer_calls_do_not_accumulate_device_memory():
+    """Init and read calls stage host buffers in scratch from the library's pool; after
+    the first cycle, further cycles leave the device's free memory where it was."""
+    torch = pytest.importorskip("torch")
+    c = case(3, 96, 96, 64, precision=lbm.LBM_FP32)
+    sh = shape(c)
+    rho = I.drop(sh, (48, 48, 32), 16, c["rho_l"], c["rho_v"], 5.0, D=3)
+    u = np.zeros((3,) + sh)
+    with lbm.Domain(lbm_params(c)) as dom:
+        dom.lbm_init_fields(rho, u)
+        dom.lbm_step(1)
+        dom.lbm_read_macroscopic()
+        dom.lbm_read_populations()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(4):
+            dom.lbm_init_fields(rho, u)
+            dom.lbm_step(1)
+            dom.lbm_read_macroscopic()
+            dom.lbm_read_populations()
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+    assert abs(free1 - free0) <= 64 << 20, (free0, free1)
+
+
 def test_macroscopic_matches_oracle():
     for D, dims in ((2, dict(nx=40, ny=30)), (3, dict(nx=17, ny=12, nz=10))):
         c = case(D, **dims)
