@@ -217,12 +217,13 @@ def test_mass_and_momentum_conserved_on_gpu(D, precision, tol):
 
 
 def _fast_patch_state(c):
-    """A drop state with a 3x3 patch moving at u_x = 0.95, where f* has negative
-    entries (1 - zeta < 0 in the rest factor), so the f*_i <= 0 guard fires there."""
+    """A drop state with a 3x3 patch of vapour, away from the drop, moving at u_x = 0.95:
+    there f* has clearly negative entries (1 - zeta < 0 in the rest factor), so the
+    f*_i <= 0 guard fires at all nine nodes in the first step."""
     sh = shape(c)
     rho = I.drop(sh, (12, 10, 0), 5, c["rho_l"], c["rho_v"], 5.0, D=2)
     u = I.rng(4).uniform(-0.02, 0.02, (2,) + sh)
-    u[0, 0, 3:6, 15:18] = 0.95
+    u[0, 0, 14:17, 1:4] = 0.95
     return I.perturbed_populations(O.init_equilibrium(oracle_params(c), rho, u), 0.01, 5)
 
 
@@ -230,18 +231,21 @@ def _fast_patch_state(c):
 def test_negative_fstar_guard_matches_oracle(precision):
     """Reading A-9: where some f*_i <= 0 the node relaxes with gamma = 2 and the guard
     counter counts it.  Both sides must take the guard at the same nodes (the counts
-    agree over two steps) and give the same populations.  The moment matrix about
-    |u| ~ 1 is less well conditioned than at rest, so the float64 bound is 1e-11."""
+    agree) and give the same populations.  The moment matrix about |u| ~ 1 is less
+    well conditioned than at rest, so the float64 bound is 1e-11.  Float32 runs one
+    step: in the second the guard also meets nodes around the patch whose smallest
+    f*_i may lie within float32 rounding of zero."""
     c = case(2, 24, 20, precision=precision)
     f0 = as_storage(_fast_patch_state(c), precision)
+    steps = 2 if precision == lbm.LBM_FP64 else 1
     with lbm.Domain(lbm_params(c)) as dom:
         dom.lbm_write_populations(f0)
-        dom.lbm_step(2)
+        dom.lbm_step(steps)
         dom.lbm_synchronize()
         fg = dom.lbm_read_populations()
         guards = dom.lbm_guard_count()
-    fo, go = O.run(oracle_params(c), f0, 2)
-    assert go > 0 and guards == go
+    fo, go = O.run(oracle_params(c), f0, steps)
+    assert go >= 9 and guards == go
     assert rel_err(fg, fo, 2).max() <= (1e-11 if precision == lbm.LBM_FP64 else 3 * TOL[lbm.LBM_FP32])
 
 
