@@ -249,6 +249,18 @@ def test_negative_fstar_guard_matches_oracle(precision):
     assert rel_err(fg, fo, 2).max() <= (1e-11 if precision == lbm.LBM_FP64 else 3 * TOL[lbm.LBM_FP32])
 
 
+@pytest.mark.parametrize("D", [2, 3])
+def test_step_from_exact_equilibrium_matches_oracle(D):
+    """From f = f^eq the higher-order part h vanishes up to rounding, so <dh|dh> is
+    tiny and gamma ill-conditioned (reading A-9); gamma multiplies h, so the result
+    is still f + f* - f^eq on both sides."""
+    dims = dict(nx=30, ny=22) if D == 2 else dict(nx=17, ny=11, nz=9)
+    c = case(D, **dims)
+    f0 = drop_state(c, perturb=0.0)
+    fg, fo = run_both(c, f0, 1)
+    assert rel_err(fg, fo, D).max() <= TOL[lbm.LBM_FP64]
+
+
 def test_nan_surfaces_as_unstable():
     c = case(2, 16, 16)
     f0 = drop_state(c)
