@@ -237,19 +237,55 @@ def laplace_measure(rho, R0):
     return r_in, r_out, Re, W
 
 
-def surface_tension_jobs(Ts, radii, kappa=0.01, nu=0.1, radii_near_tc=None, t_near=0.85):
+def surface_tension_jobs(Ts, radii, kappa=0.01, nu=0.1, radii_near_tc=None, t_near=0.85, a=WL.PAPER_EOS["a"]):
     """Static drops, entropic operator: every radius at every temperature (radii_near_tc
-    instead at T/Tc >= t_near, where the interface is wider)."""
+    instead at T/Tc >= t_near, where the interface is wider), EOS constant a."""
     jobs = []
     for T in Ts:
         for R in (radii_near_tc if (radii_near_tc and T >= t_near - 1e-12) else radii):
-            jobs.append(StudyJob(name=f"T={T:g} R={R:g}", wl=static_drop(T, nu, R=R, kappa=kappa), operator="entropic",
-                                 tags={"T": T, "R": R}))
+            jobs.append(StudyJob(name=f"a={a:g} T={T:g} R={R:g}", wl=static_drop(T, nu, R=R, kappa=kappa),
+                                 operator="entropic", a=a, tags={"T": T, "R": R, "a": a}))
     return jobs
 
 
-def surface_tension_study(quick=False):
-    """sigma(T) from the Laplace law at three radii per temperature, and the exponents."""
+# The EOS constants a of the surface-tension sweep (three values at fixed kappa, as in
+# Sec. 3.1.2; the interface width grows as sqrt(kappa/a)).
+SIGMA_A_VALUES = (0.003, 0.0017, 0.0011)
+
+
+def _sigma_rows(jobs, Ts, a):
+    """Laplace-law sigma per temperature for the drops of EOS constant a, and the
+    exponents of sigma ~ (1 - T/Tc)^m near and below T/Tc = 0.8."""
+    rows = []
+    for T in Ts:
+        pts = []
+        for r in jobs:
+            if r["tags"]["a"] == a and r["tags"]["T"] == T and r["stable"]:
+                r_in, r_out, Re, W = laplace_measure(r["rho"], r["tags"]["R"])
+                dP = pr_pressure(r_in, T, a=a) - pr_pressure(r_out, T, a=a)
+                pts.append(dict(R0=r["tags"]["R"], R_e=Re, W=W, rho_in=r_in, rho_out=r_out, dP=dP, dP_Re=dP * Re,
+                                max_u=r["final_max_u"], steps=r["steps_run"]))
+        row = dict(a=a, T_over_Tc=T, drops=pts)
+        if len(pts) >= 2:
+            # Delta P = sigma / R_e (2-D): slope of Delta P against 1/R_e
+            slope, icpt = np.polyfit([1 / p["R_e"] for p in pts], [p["dP"] for p in pts], 1)
+            row.update(sigma=float(slope), intercept=float(icpt))
+        rows.append(row)
+    fits = {}
+    for name, lo, hi in (("m_near_critical", 0.8, 1.0), ("m_below_0.8", 0.0, 0.8 + 1e-9)):
+        pts = [(1 - r["T_over_Tc"], r["sigma"]) for r in rows if "sigma" in r and r["sigma"] > 0 and lo <= r["T_over_Tc"] < hi]
+        if len(pts) >= 2:
+            fits[name] = fit_power([p[0] for p in pts], [p[1] for p in pts])[0]
+    return rows, fits
+
+
+def surface_tension_study(quick=False, a_values=None):
+    """sigma(T) from the Laplace law at three radii per temperature, for each EOS
+    constant a, and the exponents.  Radii scale with the interface width (as
+    sqrt(a0/a)) and step counts with the settling time (as a0/a: the sound speed
+    goes as sqrt(a) and the viscous time as R^2)."""
+    a0 = WL.PAPER_EOS["a"]
+    a_values = tuple(a_values or ((a0,) if quick else SIGMA_A_VALUES))
     if quick:
         groups = [((0.6, 0.75), (25.0, 40.0), 3000)]
     else:
@@ -257,36 +293,26 @@ def surface_tension_study(quick=False):
         # and the drops take longer to settle at their Laplace-shifted densities
         groups = [((0.5, 0.55, 0.6, 0.65, 0.7, 0.75, 0.8), (30.0, 45.0, 60.0), 20000),
                   ((0.85, 0.9, 0.95), (120.0, 160.0, 200.0), 100000)]
-    Ts, jobs_out, lups_s = [], [], []
-    for g_Ts, g_radii, g_steps in groups:
-        r = run_jobs(surface_tension_jobs(g_Ts, g_radii), g_steps, chunk=max(500, g_steps // 10), keep_density=True)
-        for j in r["jobs"]:
-            j["steps_run"] = g_steps
-        Ts += list(g_Ts)
-        jobs_out += r["jobs"]
-        lups_s.append(r["batched_mlups"])
-    res = dict(jobs=jobs_out, batched_mlups=min(lups_s))
-    rows = []
-    for T in Ts:
-        pts = []
-        for r in res["jobs"]:
-            if r["tags"]["T"] == T and r["stable"]:
-                r_in, r_out, Re, W = laplace_measure(r["rho"], r["tags"]["R"])
-                dP = pr_pressure(r_in, T) - pr_pressure(r_out, T)
-                pts.append(dict(R0=r["tags"]["R"], R_e=Re, W=W, rho_in=r_in, rho_out=r_out, dP=dP, dP_Re=dP * Re,
-                                max_u=r["final_max_u"], steps=r["steps_run"]))
-        row = dict(T_over_Tc=T, drops=pts)
-        if len(pts) >= 2:
-            # Delta P = sigma / R_e (2-D): slope of Delta P against 1/R_e
-            slope, icpt = np.polyfit([1 / p["R_e"] for p in pts], [p["dP"] for p in pts], 1)
-            row.update(sigma=float(slope), intercept=float(icpt))
-        rows.append(row)
-    out = dict(groups=[dict(T_over_Tc=list(g[0]), radii=list(g[1]), steps=g[2]) for g in groups], rows=rows,
-               batched_mlups=res["batched_mlups"])
-    for name, lo, hi in (("m_near_critical", 0.8, 1.0), ("m_below_0.8", 0.0, 0.8 + 1e-9)):
-        pts = [(1 - r["T_over_Tc"], r["sigma"]) for r in rows if "sigma" in r and r["sigma"] > 0 and lo <= r["T_over_Tc"] < hi]
-        if len(pts) >= 2:
-            out[name] = fit_power([p[0] for p in pts], [p[1] for p in pts])[0]
+    jobs_out, lups_s = [], []
+    for a in a_values:
+        scale = math.sqrt(a0 / a)
+        for g_Ts, g_radii, g_steps in groups:
+            radii = tuple(float(round(r * scale)) for r in g_radii)
+            steps = int(round(g_steps * a0 / a / 500.0)) * 500
+            r = run_jobs(surface_tension_jobs(g_Ts, radii, a=a), steps, chunk=max(500, steps // 10), keep_density=True)
+            for j in r["jobs"]:
+                j["steps_run"] = steps
+            jobs_out += r["jobs"]
+            lups_s.append(r["batched_mlups"])
+    Ts = [T for g in groups for T in g[0]]
+    rows, fits = [], []
+    for a in a_values:
+        ra, fa = _sigma_rows(jobs_out, Ts, a)
+        rows += ra
+        fits.append(dict(a=a, **fa))
+    out = dict(groups=[dict(T_over_Tc=list(g[0]), radii=list(g[1]), steps=g[2]) for g in groups],
+               a_values=list(a_values), rows=rows, fits=fits, batched_mlups=min(lups_s))
+    out.update({k: v for k, v in fits[0].items() if k != "a"})  # the exponents at the first a
     return out
 
 
@@ -400,13 +426,16 @@ def main():
     ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
     ap.add_argument("--workload", default=None, help="crown: a workload name (default drop2d; drop3d-paper: the paper's 3-D size)")
     ap.add_argument("--tau", type=float, default=2.0, help="crown: simulated time in convective times 2R/U")
+    ap.add_argument("--a", default=None, help="surface-tension: comma-separated EOS constants a (default 0.003,0.0017,0.0011)")
     args = ap.parse_args()
     lbm.load()
     if args.study == "crown":
         res = crown_study(args.quick, wl=WL.by_name(args.workload) if args.workload else None, t_end_tau=args.tau)
+    elif args.study == "surface-tension":
+        a_values = tuple(float(v) for v in args.a.split(",")) if args.a else None
+        res = surface_tension_study(args.quick, a_values=a_values)
     else:
-        res = {"spurious": spurious_study, "stability": stability_study,
-               "surface-tension": surface_tension_study}[args.study](args.quick)
+        res = {"spurious": spurious_study, "stability": stability_study}[args.study](args.quick)
     print(json.dumps(res), flush=True)
 
 

@@ -67,3 +67,24 @@ def test_surface_tension_jobs_cover_every_temperature_and_radius():
     assert {(j.tags["T"], j.tags["R"]) for j in jobs} == {(0.6, r) for r in (30.0, 45.0, 60.0)} | {
         (0.9, r) for r in (60.0, 90.0, 120.0)}
     assert jobs[0].wl.nx == 120 and jobs[-1].wl.nx == 480
+    small_a = S.surface_tension_jobs((0.6,), (30.0,), a=0.0011)
+    assert small_a[0].a == 0.0011 and small_a[0].tags["a"] == 0.0011 and small_a[0].eos()["a"] == 0.0011
+
+
+def test_sigma_rows_fit_the_laplace_law_per_a(monkeypatch):
+    """Stable drops whose pressure jump is exactly sigma/R_e give back sigma as the
+    slope of Delta P against 1/R_e, for the drops of the requested a only."""
+    sig = {0.6: 0.1, 0.7: 0.05}
+    jobs = [dict(tags={"a": a, "T": T, "R": R}, stable=True, rho=R, final_max_u=0.0, steps_run=1)
+            for a in (0.0017, 0.003) for T in sig for R in (30.0, 45.0, 60.0)]
+    # the inside density carries the radius; the pressure of it is sigma/R, outside 0
+    monkeypatch.setattr(S, "laplace_measure", lambda rho, R: (rho, 0.0, R, 5.0))
+    monkeypatch.setattr(S, "pr_pressure", lambda r, T, a=None: sig[T] / r if r > 0 else 0.0)
+    rows, fits = S._sigma_rows(jobs, (0.6, 0.7), 0.0017)
+    assert [r["a"] for r in rows] == [0.0017, 0.0017]
+    assert [len(r["drops"]) for r in rows] == [3, 3]
+    for r in rows:
+        assert abs(r["sigma"] - sig[r["T_over_Tc"]]) < 1e-12
+    # sigma halves from 1 - T = 0.4 to 0.3: m = ln 2 / ln(4/3)
+    import math
+    assert abs(fits["m_below_0.8"] - math.log(2) / math.log(4 / 3)) < 1e-9
