@@ -371,6 +371,40 @@ def crown_study(quick=False, wl=None, t_end_tau=2.0, samples=100, precision=lbm.
     return out
 
 
+# The paper's 2-D impacts (Sec. 3.2): (We, Re) pairs with We = 2 rho_l R0 U0^2 / sigma and
+# Re = 2 U0 R0 / nu_l, in a 24 R0 x 12 R0 box with a film h = R0, T/Tc = 0.59, nu_v = 15 nu_l.
+PAPER_2D_CASES = ((57, 4000), (93, 4000), (238, 4000), (93, 100))
+# sigma at T/Tc = 0.59 with a = 0.003 and kappa = 0.01: the Laplace-law sweep of
+# surface_tension_study gives 0.202 at 0.55 and 0.168 at 0.6; linear in between.
+SIGMA_T059 = 0.175
+
+
+def paper_2d_impacts(R0=100.0, sigma=SIGMA_T059, cases=PAPER_2D_CASES):
+    """Workloads of the paper's 2-D impact cases: U0 from We and sigma, nu_l from Re."""
+    T = 0.59
+    rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=T, **WL.PAPER_EOS))
+    out = []
+    for We, Re in cases:
+        U = math.sqrt(We * sigma / (2.0 * rl * R0))
+        nu = 2.0 * U * R0 / Re
+        out.append(WL.Workload(name=f"paper 2-D impact We={We} Re={Re} ({int(24 * R0)}x{int(12 * R0)}, R0={R0:g})",
+                               D=2, nx=int(24 * R0), ny=int(12 * R0), nz=1, T_over_Tc=T, kappa=0.01,
+                               nu_liquid=nu, mu_ratio=0.0, R=R0, U=U, film=1.0, walls_axis=1,
+                               extra={"nu_vapour_ratio": 15.0, "We": We, "Re": Re}))
+    return out
+
+
+def paper_crown_study(quick=False, t_end_tau=2.0):
+    """Crown radius series of the paper's four 2-D impact cases and their exponents."""
+    rows = []
+    for wl in paper_2d_impacts(R0=25.0 if quick else 100.0):
+        res = crown_study(wl=wl, t_end_tau=t_end_tau, samples=100)
+        rows.append(dict(We=wl.extra["We"], Re=wl.extra["Re"], U0=wl.U, nu_l=wl.nu_liquid,
+                         **{k: res[k] for k in ("tau", "t", "r", "t_contact", "fit", "failed", "seconds", "mlups",
+                                                "relaxation") if k in res}))
+    return dict(cases=rows)
+
+
 def spurious_study(quick=False):
     """The three spurious-current sweeps and the temperature exponent."""
     if quick:
@@ -424,12 +458,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["spurious", "stability", "surface-tension", "crown"])
     ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
-    ap.add_argument("--workload", default=None, help="crown: a workload name (default drop2d; drop3d-paper: the paper's 3-D size)")
+    ap.add_argument("--workload", default=None, help="crown: a workload name (default drop2d; drop3d-paper: the paper's 3-D size; paper-2d: the paper's four 2-D cases)")
     ap.add_argument("--tau", type=float, default=2.0, help="crown: simulated time in convective times 2R/U")
     ap.add_argument("--a", default=None, help="surface-tension: comma-separated EOS constants a (default 0.003,0.0017,0.0011)")
     args = ap.parse_args()
     lbm.load()
-    if args.study == "crown":
+    if args.study == "crown" and args.workload == "paper-2d":
+        res = paper_crown_study(args.quick, t_end_tau=args.tau)
+    elif args.study == "crown":
         res = crown_study(args.quick, wl=WL.by_name(args.workload) if args.workload else None, t_end_tau=args.tau)
     elif args.study == "surface-tension":
         a_values = tuple(float(v) for v in args.a.split(",")) if args.a else None

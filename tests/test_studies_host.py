@@ -88,3 +88,20 @@ def test_sigma_rows_fit_the_laplace_law_per_a(monkeypatch):
     # sigma halves from 1 - T = 0.4 to 0.3: m = ln 2 / ln(4/3)
     import math
     assert abs(fits["m_below_0.8"] - math.log(2) / math.log(4 / 3)) < 1e-9
+
+
+def test_paper_2d_impacts_reproduce_the_stated_we_and_re():
+    """Sec. 3.2: We = 2 rho_l R0 U0^2 / sigma and Re = 2 U0 R0 / nu_l recomputed from the
+    workloads give the paper's pairs; the box is 24 R0 x 12 R0 with a film of R0 and
+    nu_v = 15 nu_l."""
+    from paper_2201_12404_gb300 import lbm
+    from paper_2201_12404_gb300 import workloads as WL
+    rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=0.59, **WL.PAPER_EOS))
+    wls = S.paper_2d_impacts()
+    assert [(w.extra["We"], w.extra["Re"]) for w in wls] == list(S.PAPER_2D_CASES)
+    for w in wls:
+        assert (w.nx, w.ny, w.R, w.film * w.R) == (2400, 1200, 100.0, 100.0)
+        assert abs(2 * rl * w.R * w.U ** 2 / S.SIGMA_T059 - w.extra["We"]) < 1e-9 * w.extra["We"]
+        assert abs(2 * w.U * w.R / w.nu_liquid - w.extra["Re"]) < 1e-9 * w.extra["Re"]
+        nu_l, nu_v = WL.viscosities(w, rv, rl)
+        assert nu_v == 15 * nu_l
