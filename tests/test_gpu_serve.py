@@ -26,7 +26,7 @@ def test_mix_equals_alone_and_admission_is_continuous():
     arrivals = serve.poisson_arrivals(len(jobs), 200.0, 11)
     fps = sorted(lbm.lbm_footprint_bytes(j.params()) for j in jobs)
     budget = fps[-1] + fps[-2] + fps[0]          # a few jobs at a time
-    sample = (0, 3, 4, 7)
+    sample = (0, 3, 4, 7, 9)                     # five jobs, both lattices
     rep = serve.serve(jobs, arrivals, budget, slice_steps=50, keep_results=sample)
     assert rep["completed"] + rep["failed"] == len(jobs)
     assert rep["failed"] == 0, rep["failures"]
