@@ -71,3 +71,14 @@ def test_quick_crown_series_grows_after_contact():
     after = [x for x in r if x > 0]
     assert after[-1] > after[0]  # the crown spreads
     assert 0 <= res["relaxation"]["share_within_5pct"] <= 1
+
+
+def test_paper_2d_impact_cases_run_and_spread():
+    """The paper's four (We, Re) 2-D impacts at a quarter of its resolution (R0 = 25):
+    every case stays finite to one convective time and its crown spreads."""
+    res = S.paper_crown_study(quick=True, t_end_tau=1.0)
+    assert [(c["We"], c["Re"]) for c in res["cases"]] == list(S.PAPER_2D_CASES)
+    for c in res["cases"]:
+        assert c.get("failed") is None, c.get("failed")
+        after = [x for x in c["r"] if x > 0]
+        assert after and after[-1] > after[0]
