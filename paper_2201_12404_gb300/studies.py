@@ -401,9 +401,13 @@ def paper_2d_impacts(R0=100.0, sigma=SIGMA_T059, cases=PAPER_2D_CASES):
 
 
 def paper_crown_study(quick=False, t_end_tau=2.0):
-    """Crown radius series of the paper's four 2-D impact cases and their exponents."""
+    """Crown radius series of the paper's four 2-D impact cases and their exponents.
+    The cases run at the paper's resolution (R0 = 100: under a second each on one
+    GPU); quick stops at half a convective time."""
+    if quick:
+        t_end_tau = min(t_end_tau, 0.5)
     rows = []
-    for wl in paper_2d_impacts(R0=25.0 if quick else 100.0):
+    for wl in paper_2d_impacts():
         # the paper's square-root law is for the initial stages: fit 0.01-0.1 tau after
         # contact (samples every 0.005 tau), and report later windows beside it
         res = crown_study(wl=wl, t_end_tau=t_end_tau, samples=int(200 * t_end_tau),
