@@ -25,11 +25,16 @@
 #include "lbm_device.cuh"
 
 // Minimum resident 256-thread blocks per SM requested from the register
-// allocator in the float32 path.
+// allocator in the float32 path: three for D3Q27 (80 registers), five for D2Q9,
+// whose nine populations a node fit in 48 registers (2048x1024 impact: pass 2
+// 57.6 us per launch at three blocks, 49.5 at four, 46.9 at five).
 #ifndef LBM_K2_MINBLOCKS_F32
 #define LBM_K2_MINBLOCKS_F32 3
 #endif
-#define LBM_K2_MINBLOCKS(R) (sizeof(R) == 4 ? LBM_K2_MINBLOCKS_F32 : 1)
+#ifndef LBM_K2_MINBLOCKS_F32_2D
+#define LBM_K2_MINBLOCKS_F32_2D 5
+#endif
+#define LBM_K2_MINBLOCKS(R, D) (sizeof(R) == 4 ? ((D) == 2 ? LBM_K2_MINBLOCKS_F32_2D : LBM_K2_MINBLOCKS_F32) : 1)
 
 namespace lbm {
 
@@ -590,7 +595,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
 }
 
 template <int D, int P, typename S, typename R, typename A>
-__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
+__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R, D))
 collide_stream_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
   using H = Halo<D, BX, BY, BZ>;
@@ -630,7 +635,7 @@ __device__ __forceinline__ void stage_populations(const DevDomain& d, int x, int
 // written by that node alone within the step) and, once the force stencil of tile t
 // is done, its halo tile (TMA).
 template <int D, int P, typename S, typename R, typename A>
-__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R))
+__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R, D))
 collide_stream_persistent_kernel(DevDomain d, const __grid_constant__ TileMaps maps, int ntx, int nty, int ntiles) {
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
   constexpr int NT = BX * BY * BZ;
