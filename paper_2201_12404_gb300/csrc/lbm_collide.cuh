@@ -14,7 +14,7 @@
 //   - pass A: h = f - f^eq - s per population, the entropic sums
 //     <ds|dh> = sum s h / f*, <dh|dh> = sum h^2 / f*, and the gamma-free part
 //     g = f - omega s + f* - f^eq in place of f; h goes to shared memory,
-//   - gamma from Sec. 2.4, ratio refined to float64 accuracy,
+//   - gamma from Sec. 2.4, the float32 quotient and its residual summed in float64,
 //   - pass B: f' = g - (omega gamma/2) h, written to the A-A slots.
 // Nodes whose links all stay inside the domain take a branch with plain
 // offsets for the gather and the write; the others resolve wrap and walls.
@@ -146,17 +146,18 @@ __device__ __forceinline__ R entropic_gamma(R sA, R sB, R om) {
     return (R)(2.0 * iom - (2.0 - 2.0 * iom) * ratio);
   }
   const float A = (float)sA, B = (float)sB;
-  double ratio = 0.0;
+  float ratio = 0.0f;
   if (B > 1e-37f) {
     // the float32 quotient q and its correction e = (A - q B)/B, the residual being
-    // exact in one float32 fma, summed in float64
+    // exact in one float32 fma; q + e is formed in float64 and rounded once, which
+    // gives the ratio to within the rounding of its float32 result
     const float q = A / B;
     const float e = fmaf(-q, B, A) * __frcp_rn(B);
-    ratio = (double)q + (double)e;
+    ratio = (float)((double)q + (double)e);
   }
   // gamma/2 = 1/omega + (1/omega - 1) ratio
   const float iom = __frcp_rn((float)om);
-  return (R)(2.0f * (float)fma((double)(iom - 1.0f), ratio, (double)iom));
+  return (R)(2.0f * fmaf(iom - 1.0f, ratio, iom));
 }
 
 // Dynamic shared memory of the persistent kernel: h_i and the staged
