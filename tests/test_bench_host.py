@@ -76,3 +76,37 @@ def test_pass1_bytes_count_the_padded_auxiliary_writes():
     wl = WL.by_name("drop3d")
     pn = 516 * 516 * 260  # (512 + 4, a multiple of 4) x (512 + 4) x (256 + 4)
     assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 5 * 4
+
+
+
+def _dict_keys(node):
+    import ast
+    return {k.value for k in node.keys if isinstance(k, ast.Constant)}
+
+
+def _entry(d, key):
+    return next(v for k, v in zip(d.keys, d.values) if getattr(k, "value", None) == key)
+
+
+def test_json_lines_carry_the_contract_keys():
+    """The benchmark's JSON lines (GPU arm and reference arm) are built from dict
+    literals in bench.py: both carry the keys the benchmark contract names, and the
+    nested roofline and e2e objects carry theirs."""
+    import ast
+    src = open(bench.__file__).read()
+    tree = ast.parse(src)
+    lines = {}
+    for fn in (n for n in tree.body if isinstance(n, ast.FunctionDef) and n.name in ("run_ours", "run_reference")):
+        for node in ast.walk(fn):
+            if (isinstance(node, ast.Assign) and isinstance(node.value, ast.Dict)
+                    and any(isinstance(t, ast.Name) and t.id == "line" for t in node.targets)):
+                lines[fn.name] = node.value
+    assert set(lines) == {"run_ours", "run_reference"}
+    base = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "e2e"}
+    assert base | {"roofline", "gpu_launches", "clocks"} <= _dict_keys(lines["run_ours"])
+    assert base | {"impl", "cpu_baseline"} <= _dict_keys(lines["run_reference"])
+    assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= _dict_keys(_entry(lines["run_ours"], "roofline"))
+    for arm in lines.values():
+        assert {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"} <= _dict_keys(_entry(arm, "e2e"))
+    assert 'line["cpu_baseline"] = oracle_sample(wl)' in src
