@@ -2,7 +2,9 @@
 copy of the oracle's C source (a dropped term, a wrong sign, factor or index, a
 transposed operand), builds it into a separate library on the CPU, points the
 oracle's wrapper at it and runs the pins named for it; at least one must fail.
-The oracle itself is never modified.
+The same is done for the Python thermodynamics (the Maxwell construction), whose
+mutated copy replaces the module's functions while the pins run.  The oracle
+itself is never modified.
 
 One plausible edit is left out because no test can see it: taking the upper
 branch of the pseudo-potential sign on a tie (P = rho cs^2 exactly), a set of
@@ -126,10 +128,46 @@ def test_pins_catch_a_planted_mistake(name, old, new, catchers, tmp_path):
     assert failed, f"no pin caught the planted mistake '{name}'"
 
 
+# Mistakes planted in a copy of the oracle's Python thermodynamics (the Maxwell
+# construction and the Peng-Robinson helpers), loaded in place of the module's
+# functions for the duration of the catchers.
+PY_MUTANTS = [
+    ("equal-area integral log argument inverted", "math.log((v + b - s2 * b) / (v + b + s2 * b))",
+     "math.log((v + b + s2 * b) / (v + b - s2 * b))", [("test_maxwell_equal_area_by_quadrature", {})]),
+    ("volume cubic coefficient", "c2 = P * (2 * b - b) - R * T", "c2 = P * (2 * b) - R * T",
+     [("test_maxwell_equal_area_by_quadrature", {})]),
+    ("alpha without the square root (python)", "(1.0 - math.sqrt(T_over_Tc))", "(1.0 - T_over_Tc)",
+     [("test_oracle_pressure_matches_thermo", {})]),
+    ("coexistence densities swapped", "return 1.0 / r[-1], 1.0 / r[0], Psat", "return 1.0 / r[0], 1.0 / r[-1], Psat",
+     [("test_density_ratio_at_Tr_059_is_about_1e3", {})]),
+    ("critical pressure constant", "return 0.0778 * R * critical_temperature(a, b, R) / b",
+     "return 0.0788 * R * critical_temperature(a, b, R) / b", [("test_pr_critical_point", {})]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,catchers", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_catch_a_planted_thermodynamics_mistake(name, old, new, catchers, monkeypatch):
+    from oracle import thermo
+    src = open(thermo.__file__).read()
+    assert src.count(old) == 1, f"the text to mutate must occur once in thermo.py: {old!r}"
+    ns = {"__name__": "thermo_mutant"}
+    exec(compile(src.replace(old, new), "thermo_mutant", "exec"), ns)
+    for attr in ("alpha_of", "critical_temperature", "critical_pressure", "pressure", "maxwell"):
+        monkeypatch.setattr(thermo, attr, ns[attr])
+    failed = []
+    for pin, kwargs in catchers:
+        try:
+            with np.errstate(all="ignore"):
+                getattr(pins, pin)(**kwargs)
+        except (AssertionError, RuntimeError, FloatingPointError, ValueError, ZeroDivisionError) as e:
+            failed.append((pin, type(e).__name__))
+    assert failed, f"no pin caught the planted mistake '{name}'"
+
+
 def test_the_unmutated_oracle_passes_every_catcher():
     """The catchers fail because of the planted mistake, not by themselves."""
     seen = set()
-    for _, _, _, catchers in MUTANTS:
+    for _, _, _, catchers in MUTANTS + PY_MUTANTS:
         for pin, kwargs in catchers:
             key = (pin, tuple(sorted(kwargs.items())))
             if key in seen:
