@@ -105,3 +105,25 @@ def test_paper_2d_impacts_reproduce_the_stated_we_and_re():
         assert abs(2 * w.U * w.R / w.nu_liquid - w.extra["Re"]) < 1e-9 * w.extra["Re"]
         nu_l, nu_v = WL.viscosities(w, rv, rl)
         assert nu_v == 15 * nu_l
+
+
+def test_surface_tension_study_scales_radii_and_steps_with_a(monkeypatch):
+    """Without a GPU: the study asks for drops whose radii grow as sqrt(a0/a) (the
+    interface width at fixed kappa) and run a0/a times longer, for each a."""
+    calls = []
+
+    def fake_run(jobs, steps, chunk=500, keep_density=False, **kw):
+        calls.append((jobs, steps))
+        return dict(jobs=[dict(tags=j.tags, stable=False) for j in jobs], batched_mlups=1.0)
+
+    monkeypatch.setattr(S, "run_jobs", fake_run)
+    S.surface_tension_study(a_values=(0.003, 0.00075))
+    by_a = {}
+    for jobs, steps in calls:
+        a = jobs[0].a
+        by_a.setdefault(a, []).append((sorted({j.tags["R"] for j in jobs}), steps))
+    assert set(by_a) == {0.003, 0.00075}
+    for (r0, s0), (r1, s1) in zip(by_a[0.003], by_a[0.00075]):
+        assert r1 == [2 * r for r in r0]          # sqrt(0.003 / 0.00075) = 2
+        assert s1 == 4 * s0                        # 0.003 / 0.00075 = 4
+    assert all(j.eos()["a"] == j.a for jobs, _ in calls for j in jobs)
