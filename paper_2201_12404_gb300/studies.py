@@ -316,6 +316,18 @@ def surface_tension_study(quick=False, a_values=None):
     return out
 
 
+def crown_fits(t, r, tc, tau, windows):
+    """Exponent p and prefactor c of r = c (t - tc)^p over each window [lo, hi] of
+    t - tc, in units of tau (samples with r > 0 only; at least three per window)."""
+    fits = []
+    for lo, hi in windows:
+        pts = [(ti - tc, ri) for ti, ri in zip(t, r) if lo * tau <= ti - tc <= hi * tau and ri > 0]
+        if len(pts) >= 3:
+            p, c = fit_power([q[0] for q in pts], [q[1] for q in pts])
+            fits.append(dict(window_tau=[lo, hi], p=p, c=c, points=len(pts)))
+    return fits
+
+
 def crown_study(quick=False, wl=None, t_end_tau=2.0, samples=100, precision=lbm.LBM_FP32,
                 fit_windows=((0.05, 1.0),)):
     """Crown radius r(t) of a 2-D drop impact (entropic operator), sampled on the
@@ -366,12 +378,7 @@ def crown_study(quick=False, wl=None, t_end_tau=2.0, samples=100, precision=lbm.
     if hit:
         tc = out["t"][hit[0]]
         out["t_contact"] = tc
-        out["fits"] = []
-        for lo, hi in fit_windows:
-            pts = [(t - tc, r) for t, r in zip(out["t"], out["r"]) if lo * tau <= t - tc <= hi * tau and r > 0]
-            if len(pts) >= 3:
-                p, c = fit_power([q[0] for q in pts], [q[1] for q in pts])
-                out["fits"].append(dict(window_tau=[lo, hi], p=p, c=c, points=len(pts)))
+        out["fits"] = crown_fits(out["t"], out["r"], tc, tau, fit_windows)
         if out["fits"] and out["fits"][0]["window_tau"] == list(fit_windows[0]):
             out["fit"] = {k: v for k, v in out["fits"][0].items() if k != "window_tau"}
     return out

@@ -127,3 +127,15 @@ def test_surface_tension_study_scales_radii_and_steps_with_a(monkeypatch):
         assert r1 == [2 * r for r in r0]          # sqrt(0.003 / 0.00075) = 2
         assert s1 == 4 * s0                        # 0.003 / 0.00075 = 4
     assert all(j.eos()["a"] == j.a for jobs, _ in calls for j in jobs)
+
+
+def test_crown_fits_recover_the_exponent_of_each_window():
+    """A radius growing as 3 sqrt(t - tc) early and as (t - tc)^0.9 later is fitted
+    window by window; windows with fewer than three samples are skipped."""
+    tau, tc = 1000.0, 40.0
+    t = [tc + k * 5.0 for k in range(1, 401)]
+    r = [3 * (x - tc) ** 0.5 if x - tc <= 100 else 3 * 100 ** 0.5 * ((x - tc) / 100) ** 0.9 for x in t]
+    fits = S.crown_fits(t, r, tc, tau, ((0.01, 0.1), (0.2, 1.0), (3.0, 4.0)))
+    assert [f["window_tau"] for f in fits] == [[0.01, 0.1], [0.2, 1.0]]
+    assert abs(fits[0]["p"] - 0.5) < 1e-9 and abs(fits[0]["c"] - 3.0) < 1e-9
+    assert abs(fits[1]["p"] - 0.9) < 1e-9
