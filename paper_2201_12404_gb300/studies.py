@@ -425,6 +425,45 @@ def paper_crown_study(quick=False, t_end_tau=2.0):
     return dict(cases=rows)
 
 
+def paper_coexistence_study(temps=(0.5, 0.55, 0.59, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95), kappa=0.005,
+                            cap_steps=200000, chunk=2000, tol=1e-8, quick=False):
+    """The coexistence test of Sec. 3.1.1 in the paper's geometry: an 800 x 10 periodic
+    D2Q9 box, a 400-node liquid column in the middle, float64, entropic operator, run
+    until max |rho(t + chunk) - rho(t)| / rho_l < tol (the steady state) or cap_steps.
+    Reports the bulk densities against the Maxwell construction and the interface
+    width W = (rho_l - rho_v) / max |grad rho|."""
+    nx, ny = (200, 10) if quick else (800, 10)
+    if quick:
+        temps, cap_steps = temps[:2], min(cap_steps, 4000)
+    rows = []
+    for T in temps:
+        rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=T, **WL.PAPER_EOS))
+        wl = WL.Workload(name=f"coexistence 800x10 T/Tc={T:g}", D=2, nx=nx, ny=ny, nz=1, T_over_Tc=T, kappa=kappa,
+                         nu_liquid=0.1, mu_ratio=0.0, R=1.0, U=0.0, film=0.0)
+        rho0 = I.slab((1, ny, nx), 0, nx / 4, 3 * nx / 4, rl, rv, 5.0)
+        steps, steady, t0 = 0, False, time.perf_counter()
+        with lbm.Domain(WL.params(wl, lbm.LBM_FP64, rv=rv, rl=rl)) as dom:
+            dom.lbm_init_fields(rho0, np.zeros((2, 1, ny, nx)))
+            prev = dom.lbm_read_macroscopic()[0]
+            while steps < cap_steps:
+                dom.lbm_step(chunk)
+                steps += chunk
+                rho = dom.lbm_read_macroscopic()[0]
+                change = float(np.max(np.abs(rho - prev))) / rl
+                prev = rho
+                if change < tol:
+                    steady = True
+                    break
+            W = dom.lbm_interface_width()[0]
+        line = prev[0, ny // 2]
+        r_l = float(np.mean(line[3 * nx // 8: 5 * nx // 8]))
+        r_v = float(np.mean(np.concatenate([line[: nx // 8], line[-nx // 8:]])))
+        rows.append(dict(T_over_Tc=T, rho_l=r_l, rho_v=r_v, rho_l_maxwell=rl, rho_v_maxwell=rv,
+                         err_l=r_l / rl - 1.0, err_v=r_v / rv - 1.0, W=W, steps=steps, steady=steady,
+                         last_change=change, seconds=time.perf_counter() - t0))
+    return dict(geometry=f"{nx}x{ny}", kappa=kappa, tol=tol, rows=rows)
+
+
 def spurious_study(quick=False):
     """The three spurious-current sweeps and the temperature exponent."""
     if quick:
@@ -476,7 +515,7 @@ def stability_study(quick=False):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["spurious", "stability", "surface-tension", "crown"])
+    ap.add_argument("study", choices=["spurious", "stability", "surface-tension", "crown", "coexistence"])
     ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
     ap.add_argument("--workload", default=None, help="crown: a workload name (default drop2d; drop3d-paper: the paper's 3-D size; paper-2d: the paper's four 2-D cases)")
     ap.add_argument("--tau", type=float, default=2.0, help="crown: simulated time in convective times 2R/U")
@@ -487,6 +526,8 @@ def main():
         res = paper_crown_study(args.quick, t_end_tau=args.tau)
     elif args.study == "crown":
         res = crown_study(args.quick, wl=WL.by_name(args.workload) if args.workload else None, t_end_tau=args.tau)
+    elif args.study == "coexistence":
+        res = paper_coexistence_study(quick=args.quick)
     elif args.study == "surface-tension":
         a_values = tuple(float(v) for v in args.a.split(",")) if args.a else None
         res = surface_tension_study(args.quick, a_values=a_values)

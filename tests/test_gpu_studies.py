@@ -83,3 +83,10 @@ def test_paper_2d_impact_cases_run_and_spread():
         assert c.get("failed") is None, c.get("failed")
         after = [x for x in c["r"] if x > 0]
         assert after and after[-1] > after[0]
+
+
+def test_quick_paper_coexistence_keeps_the_liquid_at_maxwell():
+    res = S.paper_coexistence_study(quick=True)
+    assert len(res["rows"]) == 2
+    for r in res["rows"]:
+        assert abs(r["err_l"]) < 1e-2 and r["rho_v"] > 0 and r["W"] > 2
