@@ -373,18 +373,19 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     k2_ms = kms[1] / max(1, kcnt[1])
     k1_ms = kms[0] / max(1, kcnt[0])
+    Q = 27 if wl.D == 3 else 9
+    full_fp32 = args.precision == "fp32" and wl.N == 512 * 512 * 256
     k2_bytes = algorithmic_bytes_k2(wl, pop_bytes, 8 if pop_bytes == 8 else 4)
     if args.precision == "fp16dev":
         k2_bytes += wl.N * 8  # writer densities: one read (the neighbours' are cache hits), one write
-    achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
     k1_bytes = algorithmic_bytes_k1(wl, pop_bytes, 8 if pop_bytes == 8 else 4)
     if args.precision == "fp16dev":
         k1_bytes += wl.N * 4  # writer densities read by the decode
-    step_achieved = (k1_bytes + k2_bytes) / ((k1_ms + k2_ms) * 1e-3) / 1e9
-    full_fp32 = args.precision == "fp32" and wl.N == 512 * 512 * 256
     traffic = recorded_traffic("d3q27_fp32_collide_stream") if full_fp32 else None
     traffic_k1 = recorded_traffic("d3q27_fp32_moments_eos") if full_fp32 else None
-    Q = 27 if wl.D == 3 else 9
+    achieved = k2_bytes / (k2_ms * 1e-3) / 1e9
+    step_achieved = (k1_bytes + k2_bytes) / ((k1_ms + k2_ms) * 1e-3) / 1e9
+    both = traffic is not None and traffic_k1 is not None
     metric, config = metric_and_config(args, wl, world)
     line = {
         "metric": metric,
@@ -398,14 +399,14 @@ def run_ours(args):
                      "kernel": "collide_stream (force + collide + stream)",
                      "algorithmic_bytes_per_launch": k2_bytes,
                      "kernel_ms": k2_ms},
-        # the fused step, both passes together: their algorithmic bytes (and the
+        # the whole step, all its kernels together: their algorithmic bytes (and the
         # recorded DRAM bytes) over their summed CUDA-event times
         "step_roofline": {"kernels": "moments_eos + collide_stream", "unit": "GB/s", "peak": hbm,
                           "achieved": step_achieved, "frac": step_achieved / hbm,
                           "algorithmic_bytes_per_step": k1_bytes + k2_bytes,
-                          "traffic_per_step": (traffic + traffic_k1) if (traffic and traffic_k1) else None,
+                          "traffic_per_step": (traffic + traffic_k1) if both else None,
                           "dram_frac": ((traffic + traffic_k1) / ((k1_ms + k2_ms) * 1e-3) / 1e9 / hbm)
-                          if (traffic and traffic_k1) else None,
+                          if both else None,
                           "bytes_per_lup_floor": 2 * Q * pop_bytes,
                           "frac_of_floor": mlups / world * 1e6 * 2 * Q * pop_bytes / (hbm * 1e9),
                           "moments_eos_ms": k1_ms, "collide_stream_ms": k2_ms},

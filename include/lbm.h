@@ -80,6 +80,7 @@ typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 } lbm_bc;
  * relaxes the higher-order moments fully onto f*). */
 typedef enum { LBM_GAMMA_ENTROPIC = 0, LBM_GAMMA_FIXED = 1 } lbm_gamma_mode;
 
+
 typedef struct {
   int32_t lattice;     /* lbm_lattice */
   int32_t precision;   /* lbm_precision */
@@ -102,12 +103,24 @@ typedef struct {
    * 2 = float64 everywhere. */
   int32_t eos_fp64;
   void* stream;         /* cudaStream_t to run on; NULL = a stream the library creates */
+  /* Optional device allocator for the buffers a domain keeps for its lifetime
+   * (populations, auxiliary fields, error words, the gamma record), for example
+   * a framework's caching allocator; NULL dev_alloc = cudaMalloc/cudaFree.  Set
+   * both or neither.  dev_alloc(bytes, alloc_ctx) returns memory of the current
+   * device aligned to 256 bytes, or NULL when it cannot (lbm_create_domain then
+   * fails with LBM_ERR_OOM); dev_free(ptr, alloc_ctx) releases it and is called
+   * from lbm_destroy after the domain's stream has been synchronised, on the
+   * same host thread as other calls on the handle.  Scratch memory of the calls
+   * that take host buffers still comes from the library's own pool. */
+  void* (*dev_alloc)(size_t bytes, void* alloc_ctx);
+  void (*dev_free)(void* ptr, void* alloc_ctx);
+  void* alloc_ctx;
 } lbm_params;
 
 /* Fill p with defaults: D2Q9 FP32 64x64, the paper's EOS constants
  * (a = 0.003, b = 0.095, R = 1, w' = 0.344, Sec. 3.1), T/Tc = 0.8, kappa = 0,
  * nu = 0.1, rho_liquid = 1, rho_vapour = 0.5, periodic, entropic gamma,
- * eos_fp64 = 1, NULL stream. */
+ * eos_fp64 = 1, NULL stream, no allocator. */
 lbm_status lbm_default_params(lbm_params* p);
 
 /* Validate p, allocate the domain's device memory and create its handle.

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -56,6 +57,7 @@ std::string validate(const lbm_params* p) {
   if (p->gamma_mode != LBM_GAMMA_ENTROPIC && p->gamma_mode != LBM_GAMMA_FIXED) return "gamma_mode must be 0 or 1";
   if (p->gamma_mode == LBM_GAMMA_FIXED && !std::isfinite(p->gamma_value)) return "gamma_value must be finite";
   if (p->eos_fp64 < 0 || p->eos_fp64 > 2) return "eos_fp64 must be 0, 1 or 2";
+  if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr)) return "set both dev_alloc and dev_free, or neither";
   return "";
 }
 
@@ -134,6 +136,26 @@ cudaError_t scratch_alloc(lbm_domain* h, T** p, size_t bytes) {
   cudaMemPool_t pool = scratch_pool();
   if (!pool) return cudaMallocAsync((void**)p, bytes, h->stream);
   return cudaMallocFromPoolAsync((void**)p, bytes, pool, h->stream);
+}
+
+// Device memory a domain keeps for its lifetime: the caller's allocator when
+// lbm_params sets one, cudaMalloc otherwise.
+cudaError_t keep_alloc(const lbm_params& p, void** ptr, size_t bytes) {
+  if (!p.dev_alloc) return cudaMalloc(ptr, bytes);
+  *ptr = p.dev_alloc(bytes, p.alloc_ctx);
+  if (!*ptr) return cudaErrorMemoryAllocation;
+  if ((uintptr_t)*ptr % 256 != 0) {
+    p.dev_free(*ptr, p.alloc_ctx);
+    *ptr = nullptr;
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+void keep_free(const lbm_params& p, void* ptr) {
+  if (!ptr) return;
+  if (p.dev_alloc) p.dev_free(ptr, p.alloc_ctx);
+  else cudaFree(ptr);
 }
 
 #define LBM_LIVE(h)                                                               \
@@ -304,7 +326,7 @@ lbm_status lbm_default_params(lbm_params* p) {
 size_t lbm_footprint_bytes(const lbm_params* p) {
   if (!validate(p).empty()) return 0;
   Sizes s = sizes_of(*p, ops_for(*p));
-  return s.f_bytes + s.aux_bytes + s.rho_w_bytes + sizeof(unsigned int) + sizeof(unsigned long long);
+  return s.f_bytes + s.aux_bytes + s.rho_w_bytes + sizeof(unsigned int) + 2 * sizeof(unsigned long long);
 }
 
 lbm_status lbm_psi_sign_changes(const lbm_params* p, double changes[3], int* n, double* s0) {
@@ -409,15 +431,21 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
     if ((err = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(err, "cudaStreamCreate");
     h->own_stream = true;
   }
-  if ((err = cudaMalloc(&d.f, s.f_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(populations)");
-  if ((err = cudaMalloc(&d.aux, s.aux_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(aux)");
+  if ((err = keep_alloc(*p, &d.f, s.f_bytes)) != cudaSuccess) return bail(err, "allocating the populations");
+  if ((err = keep_alloc(*p, &d.aux, s.aux_bytes)) != cudaSuccess) return bail(err, "allocating the auxiliary fields");
   if (s.rho_w_bytes) {
-    if ((err = cudaMalloc(&d.rho_w[0], s.rho_w_bytes)) != cudaSuccess) return bail(err, "cudaMalloc(rho_w)");
+    void* rw = nullptr;
+    if ((err = keep_alloc(*p, &rw, s.rho_w_bytes)) != cudaSuccess) return bail(err, "allocating rho_w");
+    d.rho_w[0] = (float*)rw;
     d.rho_w[1] = d.rho_w[0] + s.N;
     if ((err = cudaMemsetAsync(d.rho_w[0], 0, s.rho_w_bytes, h->stream)) != cudaSuccess) return bail(err, "cudaMemset(rho_w)");
   }
-  if ((err = cudaMalloc(&d.flags, sizeof(unsigned int) + sizeof(unsigned long long) * 2)) != cudaSuccess)
-    return bail(err, "cudaMalloc(flags)");
+  {
+    void* fl = nullptr;
+    if ((err = keep_alloc(*p, &fl, sizeof(unsigned int) + sizeof(unsigned long long) * 2)) != cudaSuccess)
+      return bail(err, "allocating the error words");
+    d.flags = (unsigned int*)fl;
+  }
   d.guards = (unsigned long long*)((char*)d.flags + sizeof(unsigned long long));
   if ((err = cudaMemsetAsync(d.flags, 0, sizeof(unsigned int) + sizeof(unsigned long long) * 2, h->stream)) != cudaSuccess)
     return bail(err, "cudaMemset(flags)");
@@ -443,11 +471,11 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
-  if (h->dev.f) cudaFree(h->dev.f);
-  if (h->dev.aux) cudaFree(h->dev.aux);
-  if (h->dev.rho_w[0]) cudaFree(h->dev.rho_w[0]);
-  if (h->dev.flags) cudaFree(h->dev.flags);
-  if (h->dev.gamma_out) cudaFree(h->dev.gamma_out);
+  keep_free(h->p, h->dev.f);
+  keep_free(h->p, h->dev.aux);
+  keep_free(h->p, h->dev.rho_w[0]);
+  keep_free(h->p, h->dev.flags);
+  keep_free(h->p, h->dev.gamma_out);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->flags_ev) cudaEventDestroy(h->flags_ev);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -515,7 +543,9 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
   if (st != LBM_OK) return st;
   if (h->record_gamma && !h->dev.gamma_out) {
     // (gamma, omega) per node
-    LBM_CUDA(h, cudaMalloc(&h->dev.gamma_out, 2 * (size_t)h->dev.N * sizeof(float)));
+    void* g = nullptr;
+    LBM_CUDA(h, keep_alloc(h->p, &g, 2 * (size_t)h->dev.N * sizeof(float)));
+    h->dev.gamma_out = (float*)g;
     LBM_CUDA(h, cudaMemsetAsync(h->dev.gamma_out, 0, 2 * (size_t)h->dev.N * sizeof(float), h->stream));
   }
   if (h->record_gamma && nsteps > 0) h->gamma_recorded = true;

@@ -216,91 +216,26 @@ struct NoHooks {
   __device__ void aux() const {}
 };
 
-// One tile of pass 2 whose origin is (x0, y0, z0), run by the BX*BY*BZ threads of
-// the block.  kTma: the halo tile and the q boxes (s_q) come from TMA copies of
-// the tensor maps `maps`, completed on `bar` (phase `phase`); otherwise each warp
-// loads halo rows and q comes from global memory.
-// kStaged (with kTma): the caller has already issued this tile's halo copy and
-// staged its populations in s_f ([i][thread], cp.async completed); once every
-// thread has read its populations the tile calls hooks.prefetch() (the next
-// tile's populations into s_f), and once the block is done with the halo tile it
-// calls hooks.aux() (the next halo copy into s_aux) after a block barrier that
-// every thread of the block reaches.
-// s_aux holds the HN (rho, psi) pairs of the halo tile; s_h Q*BX*BY*BZ values of h:
-// the pair rows first (Two<R> [pair*3 + ix][thread]), then the single row.
-// Returns false when the halo copy did not arrive within the poll limit.
-template <int D, int BX, int BY, int BZ, int P, typename S, typename R, typename A, bool kTma,
-          bool kStaged = false, typename Hooks = NoHooks>
-__device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps* maps, int x0, int y0, int z0,
-                                             Two<A>* s_aux, A* s_q, R* s_h, unsigned long long* bar, uint32_t phase,
-                                             const S* s_f = nullptr, const Hooks& hooks = Hooks()) {
-  constexpr int Q = Lattice<D>::Q;
-  constexpr int NT = BX * BY * BZ;
-  constexpr int HX = Halo<D, BX, BY, BZ>::HX, HY = Halo<D, BX, BY, BZ>::HY, HZ = Halo<D, BX, BY, BZ>::HZ;
-  constexpr int HN = HX * HY * HZ;
+// Moments of one node: rho, j and the second moments Pi.
+template <typename R> struct NodeMoments {
+  R rho, jx, jy, jz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
+};
+
+// Pairs the rows of the node's populations f (fp: pairs, fs: the single row,
+// indexed by ix = cx + 1) and forms rho, j, Pi from row sums:
+// r0 = f- + f0 + f+, r1 = f+ - f-, r2 = f+ + f-.
+template <int D, typename R>
+__device__ __forceinline__ void row_moments(const R (&f)[Lattice<D>::Q], Two<R> (&fp)[RowPairs<D>::kPairs][3],
+                                            R (&fs)[3], NodeMoments<R>& m) {
   constexpr int NY = RowPairs<D>::kYPairs, NP = RowPairs<D>::kPairs;
   using RP = RowPairs<D>;
   using R2 = Two<R>;
-  constexpr R cs2 = (R)(1.0 / 3.0);
-  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
-  const Phys<R>& ph = phys<R>(d);
-  R2* s_h2 = (R2*)s_h;                  // [NP * 3][NT]
-  R* s_h1 = s_h + 2 * (NP * 3) * NT;    // [3][NT]
-
-  // ---- stage (rho, psi) of the tile plus halo; padded coordinates of the halo
-  //      origin are the tile origin itself
-  if (kTma && !kStaged) {
-    // x0 is a multiple of BX (>= 32), so the box starts 16-byte aligned
-    if (tid == 0) tma_load_fields<D, BX, BY, BZ, A>(maps, s_aux, s_q, bar, x0, y0, z0);
-  } else if (!kTma) {
-    const Two<A>* a2 = (const Two<A>*)d.aux;
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int r = warp; r < HY * HZ; r += NT / 32) {
-      const int yp = y0 + r % HY, zp = z0 + r / HY;
-      const bool row_ok = yp < d.py && zp < d.pz;
-      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
-      for (int hx = lane; hx < HX; hx += 32) {
-        const bool ok = row_ok && x0 + hx < d.px;
-        s_aux[r * HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
-      }
-    }
-    __syncthreads();
-  }
-
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
-  const bool active = x < d.nx && y < d.ny && z < d.nz;
-  const long long n = node_of(d, x, y, z);
-  const bool fast = P == 0 || fast_links<D>(d, x, y, z);
-
-  R f[Q];
-  if (kStaged) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = active ? ld_pop<S, R>(s_f + i * NT + tid) : (R)wq<D>(i);
-  } else if (active) {
-    gather<D, P, S, R>(d, x, y, z, f);
-  }
-  bool tile_ok = true;
-  if (kTma) {
-    // every thread waits, so that the block cannot retire while the copy is in flight
-    tile_ok = mbar_wait_bounded(bar, phase, kTileWaitPolls);
-    if (!kStaged && !tile_ok) {
-      if (tid == 0) atomicOr(d.flags, 2u);
-      mbar_wait_bounded(bar, phase, kTileWaitPolls);
-      return false;
-    }
-  }
-  if (!kStaged && !active) return true;
-
-  R2 fp[NP][3];
-  R fs[3];
 #pragma unroll
   for (int ix = 0; ix < 3; ++ix) {
 #pragma unroll
     for (int k = 0; k < NP; ++k) fp[k][ix] = two<R>(f[RP::pop(k, 0, ix)], f[RP::pop(k, 1, ix)]);
     fs[ix] = f[RP::single(ix)];
   }
-
-  // ---- rho, j, Pi from row sums: r0 = f- + f0 + f+, r1 = f+ - f-, r2 = f+ + f-
   const R2 zero2 = both<R>((R)0), sgn = two<R>((R)-1, (R)1);
   R2 RHO = zero2, JX = zero2, PXX = zero2, JY = zero2, PXY = zero2, PYY = zero2;
   R2 JZ = zero2, PXZ = zero2, PZZ = zero2, PYZ = zero2;
@@ -320,37 +255,39 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     }
   }
   const R s2 = fs[0] + fs[2], s0 = s2 + fs[1], s1 = fs[2] - fs[0];
-  const R rho = (RHO.x + RHO.y) + s0;
-  const R jx = (JX.x + JX.y) + s1, Pxx = (PXX.x + PXX.y) + s2;
-  const R jy = JY.x + JY.y, Pxy = PXY.x + PXY.y, Pyy = PYY.x + PYY.y;
-  const R jz = D == 3 ? JZ.x + JZ.y : (R)0, Pxz = D == 3 ? PXZ.x + PXZ.y : (R)0;
-  const R Pzz = D == 3 ? PZZ.x + PZZ.y : (R)0, Pyz = D == 3 ? PYZ.x + PYZ.y : (R)0;
-  const R inv_rho = (R)1 / rho;
-  const R u[3] = {jx * inv_rho, jy * inv_rho, jz * inv_rho};
-  // every staged population has been consumed: s_f may take the next tile's
-  if (kStaged) hooks.prefetch();
+  m.rho = (RHO.x + RHO.y) + s0;
+  m.jx = (JX.x + JX.y) + s1;
+  m.Pxx = (PXX.x + PXX.y) + s2;
+  m.jy = JY.x + JY.y; m.Pxy = PXY.x + PXY.y; m.Pyy = PYY.x + PYY.y;
+  m.jz = D == 3 ? JZ.x + JZ.y : (R)0;
+  m.Pxz = D == 3 ? PXZ.x + PXZ.y : (R)0;
+  m.Pzz = D == 3 ? PZZ.x + PZZ.y : (R)0;
+  m.Pyz = D == 3 ? PYZ.x + PYZ.y : (R)0;
+}
 
-  // ---- force: dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g, sums over the
-  //      lattice links row by row with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz).  The
-  //      two lanes carry G3[rho] (x) and G4[psi] (y): a link term 2 rho(r+c) - rho(r+2c)
-  //      and (4/3) psi(r+c) - (1/6) psi(r+2c) is (2, 4/3) times v(r+c) + (-1/2, -1/8) v(r+2c),
-  //      the common (2, 4/3) applied once at the end.
-  const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
-  //      Rows are summed by weight class (w_y w_z: centre 2 (2/3), edge 1/2 (2/3) or
-  //      2 (1/6), corner 1/2 (1/6); 2-D: 2, 1/2) and the weights applied once: GX =
-  //      (1/6) sum w_yz (t(+1) - t(-1)), and the y/z components use u = t(-1) + t(+1) +
-  //      4 t(0) = 6 x (the row's weighted sum over cx).
+// Force of Eq. (Kforce_final) with the physical sign, plus rho g:
+// dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g, from the (rho, psi) pairs
+// at(dx, dy, dz) of the node's radius-2 stencil (at(0, 0, 0) the node itself).
+// The lattice links are summed row by row with weights w_i/cs^2 = 3 w(cx) w(cy) w(cz).
+// The two lanes carry G3[rho] (x) and G4[psi] (y): a link term 2 rho(r+c) - rho(r+2c)
+// and (4/3) psi(r+c) - (1/6) psi(r+2c) is (2, 4/3) times v(r+c) + (-1/2, -1/8) v(r+2c),
+// the common (2, 4/3) applied once at the end.  Rows are summed by weight class
+// (w_y w_z: centre 2 (2/3), edge 1/2 (2/3) or 2 (1/6), corner 1/2 (1/6); 2-D: 2,
+// 1/2) and the weights applied once: GX = (1/6) sum w_yz (t(+1) - t(-1)), and the
+// y/z components use u = t(-1) + t(+1) + 4 t(0) = 6 x (the row's weighted sum over cx).
+template <int D, typename R, typename A, typename AuxAt>
+__device__ __forceinline__ void stencil_force(const Phys<R>& ph, R rho, const AuxAt& at, R (&F)[3]) {
+  constexpr int Q = Lattice<D>::Q;
+  using R2 = Two<R>;
+  const R2 zero2 = both<R>((R)0);
   const R2 cb = two<R>((R)-0.5, (R)-0.125), four = both<R>((R)4);
+  auto v = [](const Two<A>& a) { return two<R>((R)a.x, (R)a.y); };
   R2 DXc = zero2, DXe = zero2, DXk = zero2, YE = zero2, YK = zero2, ZE = zero2, ZK = zero2;
 #pragma unroll
   for (int row = 0; row < Q / 3; ++row) {
     const int cy = row % 3 - 1, cz = D == 3 ? row / 3 - 1 : 0;
-    const int orow = HX * (cy + HY * cz);
-    const Two<A>* p1 = s_aux + sc + orow;
-    const Two<A>* p2 = s_aux + sc + 2 * orow;
-    auto v = [](const Two<A>& a) { return two<R>((R)a.x, (R)a.y); };
-    const R2 tm = fma2(cb, v(p2[-2]), v(p1[-1]));
-    const R2 tp = fma2(cb, v(p2[2]), v(p1[1]));
+    const R2 tm = fma2(cb, v(at(-2, 2 * cy, 2 * cz)), v(at(-1, cy, cz)));
+    const R2 tp = fma2(cb, v(at(2, 2 * cy, 2 * cz)), v(at(1, cy, cz)));
     const R2 dx = sub2(tp, tm);
     if (cy == 0 && cz == 0) {
       DXc = add2(DXc, dx);  // the centre row adds nothing to the y and z components
@@ -358,7 +295,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     }
     if (cy != 0 && cz != 0) DXk = add2(DXk, dx);
     else DXe = add2(DXe, dx);
-    const R2 u = fma2(four, fma2(cb, v(p2[0]), v(p1[0])), add2(tp, tm));
+    const R2 u = fma2(four, fma2(cb, v(at(0, 2 * cy, 2 * cz)), v(at(0, cy, cz))), add2(tp, tm));
     if (cy != 0) {
       R2& acc = cz == 0 ? YE : YK;
       acc = cy > 0 ? add2(acc, u) : sub2(acc, u);
@@ -375,55 +312,34 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   const R2 GX = fma2(both<R>(wc), DXc, fma2(both<R>(we), DXe, mul2(both<R>(wk), DXk)));
   const R2 GY = fma2(both<R>(we), YE, mul2(both<R>(wk), YK));
   const R2 GZ = fma2(both<R>(we), ZE, mul2(both<R>(wk), ZK));
-  // s psi at the node: psi from the tile, s from the node's density in the tile
-  const Two<A> c_aux = s_aux[sc];
+  // s psi at the node: psi from the stencil, s from the node's density there
+  const Two<A> c_aux = at(0, 0, 0);
   const R spsi_c = psi_sign<R>(ph, (R)c_aux.x) * (R)c_aux.y;
   const R2 wf = two<R>((R)2 * ph.kappa * rho, (R)(8.0 / 3.0) * spsi_c);  // (kappa rho, 2 s psi) * (2, 4/3)
-  R F[3];
-  {
-    const R2 tx = mul2(wf, GX), ty = mul2(wf, GY), tz = mul2(wf, GZ);
-    F[0] = rho * ph.g[0] - (tx.x + tx.y);
-    F[1] = rho * ph.g[1] - (ty.x + ty.y);
-    F[2] = D == 3 ? rho * ph.g[2] - (tz.x + tz.y) : (R)0;
-  }
+  const R2 tx = mul2(wf, GX), ty = mul2(wf, GY), tz = mul2(wf, GZ);
+  F[0] = rho * ph.g[0] - (tx.x + tx.y);
+  F[1] = rho * ph.g[1] - (ty.x + ty.y);
+  F[2] = D == 3 ? rho * ph.g[2] - (tz.x + tz.y) : (R)0;
+}
 
-  // ---- Phi_aa = -(1 - omega/2) d_a q_a, central difference.  The sign is the one
-  // that cancels the lattice's third-moment defect (sum f^eq c_a^3 = rho u_a where
-  // rho u_a^3 + 3 P0 u_a is due) in the diagonal momentum flux, the purpose Sec. 2.2
-  // gives Phi; Eq. (correction) prints the opposite sign, which doubles the defect.
-  const R om = omega_of<R>(ph, rho);
-  R Phi[3] = {0, 0, 0};
-  if (kTma) {
-    using H = Halo<D, BX, BY, BZ>;
-    const int qc = (threadIdx.x + 2) + H::QX * ((threadIdx.y + 1) + H::QY * (D == 3 ? threadIdx.z + 1 : 0));
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const A* qa = s_q + a * H::template qstride<A>() + qc;
-      const int e = a == 0 ? 1 : (a == 1 ? H::QX : H::QX * H::QY);
-      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[-e] - (R)qa[e]) * (R)0.5;
-    }
-  } else {
-    const A* a_q = (const A*)d.aux + 2 * d.PN;
-    const long long pc = pnode_of<D>(d, x, y, z);
-    const long long sy = d.px, sz = (long long)d.px * d.py;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const A* qa = a_q + a * d.PN;
-      const long long e = a == 0 ? 1 : (a == 1 ? sy : sz);
-      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc - e] - (R)qa[pc + e]) * (R)0.5;
-    }
-  }
-  if (kStaged) {
-    // the block is done with the staged fields (a block-wide vote on the copy's arrival)
-    if (__syncthreads_or(!tile_ok)) {
-      if (tid == 0) atomicOr(d.flags, 2u);
-      mbar_wait_bounded(bar, phase, kTileWaitPolls);
-      return false;
-    }
-    hooks.aux();
-    if (!active) return true;
-  }
-
+// Equilibria, k/s/h split, gamma and relaxation of one node (Eq. LBGK with the
+// entropic mirror state of Sec. 2.4): fp/fs hold the node's pre-collision
+// populations in row pairs on entry and its post-collision populations on exit.
+// m: the node's moments, u = j/rho, F the force (times dt), Phi the diagonal
+// correction, om the local omega; s_h holds h_i of the NT threads of the block
+// ([i][thread]), n is the node (for the guard count and the gamma record).
+template <int D, typename R, int NT>
+__device__ __forceinline__ void collide_relax(const DevDomain& d, const Phys<R>& ph, long long n,
+                                              const NodeMoments<R>& m, R inv_rho, const R (&u)[3], const R (&F)[3],
+                                              const R (&Phi)[3], R om, Two<R> (&fp)[RowPairs<D>::kPairs][3],
+                                              R (&fs)[3], R* s_h, int tid) {
+  constexpr int NY = RowPairs<D>::kYPairs, NP = RowPairs<D>::kPairs;
+  using R2 = Two<R>;
+  constexpr R cs2 = (R)(1.0 / 3.0);
+  const R rho = m.rho;
+  const R2 zero2 = both<R>((R)0);
+  R2* s_h2 = (R2*)s_h;                  // [NP * 3][NT]
+  R* s_h1 = s_h + 2 * (NP * 3) * NT;    // [3][NT]
   // ---- one-dimensional factors per axis, index k = c+1: equilibrium E, extended
   //      equilibrium St, first-order dual d1 of the central Hermite basis (the
   //      second-order dual is d2 = {1/2, -1, 1/2})
@@ -446,12 +362,12 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   for (int k = 0; k < 3; ++k) { E[k] = Ef(0, k); St[k] = Sf(0, k); D1[k] = Df(0, k); }
   // second-order central Hermite moments; the shear part keeps the off-diagonals
   // and the deviatoric diagonal a_aa - trace/D
-  const R axy = Pxy - rho * u[0] * u[1];
-  const R axz = D == 3 ? Pxz - rho * u[0] * u[2] : (R)0;
-  const R ayz = D == 3 ? Pyz - rho * u[1] * u[2] : (R)0;
-  const R adx = Pxx - rho * u[0] * u[0] - rho * cs2;
-  const R ady = Pyy - rho * u[1] * u[1] - rho * cs2;
-  const R adz = D == 3 ? Pzz - rho * u[2] * u[2] - rho * cs2 : (R)0;
+  const R axy = m.Pxy - rho * u[0] * u[1];
+  const R axz = D == 3 ? m.Pxz - rho * u[0] * u[2] : (R)0;
+  const R ayz = D == 3 ? m.Pyz - rho * u[1] * u[2] : (R)0;
+  const R adx = m.Pxx - rho * u[0] * u[0] - rho * cs2;
+  const R ady = m.Pyy - rho * u[1] * u[1] - rho * cs2;
+  const R adz = D == 3 ? m.Pzz - rho * u[2] * u[2] - rho * cs2 : (R)0;
   const R tr = (adx + ady + adz) * (R)(1.0 / D);
   const R devx = adx - tr, devy = ady - tr, devz = D == 3 ? adz - tr : (R)0;
 
@@ -563,6 +479,133 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     for (int ix = 0; ix < 3; ++ix) fp[k][ix] = fma2(mch, s_h2[(3 * k + ix) * NT + tid], fp[k][ix]);
 #pragma unroll
   for (int ix = 0; ix < 3; ++ix) fs[ix] -= ch * s_h1[ix * NT + tid];
+
+}
+
+// One tile of pass 2 whose origin is (x0, y0, z0), run by the BX*BY*BZ threads of
+// the block.  kTma: the halo tile and the q boxes (s_q) come from TMA copies of
+// the tensor maps `maps`, completed on `bar` (phase `phase`); otherwise each warp
+// loads halo rows and q comes from global memory.
+// kStaged (with kTma): the caller has already issued this tile's halo copy and
+// staged its populations in s_f ([i][thread], cp.async completed); once every
+// thread has read its populations the tile calls hooks.prefetch() (the next
+// tile's populations into s_f), and once the block is done with the halo tile it
+// calls hooks.aux() (the next halo copy into s_aux) after a block barrier that
+// every thread of the block reaches.
+// s_aux holds the HN (rho, psi) pairs of the halo tile; s_h Q*BX*BY*BZ values of h:
+// the pair rows first (Two<R> [pair*3 + ix][thread]), then the single row.
+// Returns false when the halo copy did not arrive within the poll limit.
+template <int D, int BX, int BY, int BZ, int P, typename S, typename R, typename A, bool kTma,
+          bool kStaged = false, typename Hooks = NoHooks>
+__device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps* maps, int x0, int y0, int z0,
+                                             Two<A>* s_aux, A* s_q, R* s_h, unsigned long long* bar, uint32_t phase,
+                                             const S* s_f = nullptr, const Hooks& hooks = Hooks()) {
+  constexpr int Q = Lattice<D>::Q;
+  constexpr int NT = BX * BY * BZ;
+  constexpr int HX = Halo<D, BX, BY, BZ>::HX, HY = Halo<D, BX, BY, BZ>::HY, HZ = Halo<D, BX, BY, BZ>::HZ;
+  constexpr int NP = RowPairs<D>::kPairs;
+  using RP = RowPairs<D>;
+  using R2 = Two<R>;
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  const Phys<R>& ph = phys<R>(d);
+
+  // ---- stage (rho, psi) of the tile plus halo; padded coordinates of the halo
+  //      origin are the tile origin itself
+  if (kTma && !kStaged) {
+    // x0 is a multiple of BX (>= 32), so the box starts 16-byte aligned
+    if (tid == 0) tma_load_fields<D, BX, BY, BZ, A>(maps, s_aux, s_q, bar, x0, y0, z0);
+  } else if (!kTma) {
+    const Two<A>* a2 = (const Two<A>*)d.aux;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < HY * HZ; r += NT / 32) {
+      const int yp = y0 + r % HY, zp = z0 + r / HY;
+      const bool row_ok = yp < d.py && zp < d.pz;
+      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
+      for (int hx = lane; hx < HX; hx += 32) {
+        const bool ok = row_ok && x0 + hx < d.px;
+        s_aux[r * HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
+      }
+    }
+    __syncthreads();
+  }
+
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
+  const bool active = x < d.nx && y < d.ny && z < d.nz;
+  const long long n = node_of(d, x, y, z);
+  const bool fast = P == 0 || fast_links<D>(d, x, y, z);
+
+  R f[Q];
+  if (kStaged) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = active ? ld_pop<S, R>(s_f + i * NT + tid) : (R)wq<D>(i);
+  } else if (active) {
+    gather<D, P, S, R>(d, x, y, z, f);
+  }
+  bool tile_ok = true;
+  if (kTma) {
+    // every thread waits, so that the block cannot retire while the copy is in flight
+    tile_ok = mbar_wait_bounded(bar, phase, kTileWaitPolls);
+    if (!kStaged && !tile_ok) {
+      if (tid == 0) atomicOr(d.flags, 2u);
+      mbar_wait_bounded(bar, phase, kTileWaitPolls);
+      return false;
+    }
+  }
+  if (!kStaged && !active) return true;
+
+  R2 fp[NP][3];
+  R fs[3];
+  NodeMoments<R> m;
+  row_moments<D, R>(f, fp, fs, m);
+  const R rho = m.rho;
+  const R inv_rho = (R)1 / rho;
+  const R u[3] = {m.jx * inv_rho, m.jy * inv_rho, m.jz * inv_rho};
+  // every staged population has been consumed: s_f may take the next tile's
+  if (kStaged) hooks.prefetch();
+
+  // ---- force from the staged (rho, psi) halo tile
+  const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
+  R F[3];
+  stencil_force<D, R, A>(ph, rho, [&](int dx, int dy, int dz) { return s_aux[sc + dx + HX * (dy + HY * dz)]; }, F);
+
+  // ---- Phi_aa = -(1 - omega/2) d_a q_a, central difference.  The sign is the one
+  // that cancels the lattice's third-moment defect (sum f^eq c_a^3 = rho u_a where
+  // rho u_a^3 + 3 P0 u_a is due) in the diagonal momentum flux, the purpose Sec. 2.2
+  // gives Phi; Eq. (correction) prints the opposite sign, which doubles the defect.
+  const R om = omega_of<R>(ph, rho);
+  R Phi[3] = {0, 0, 0};
+  if (kTma) {
+    using H = Halo<D, BX, BY, BZ>;
+    const int qc = (threadIdx.x + 2) + H::QX * ((threadIdx.y + 1) + H::QY * (D == 3 ? threadIdx.z + 1 : 0));
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const A* qa = s_q + a * H::template qstride<A>() + qc;
+      const int e = a == 0 ? 1 : (a == 1 ? H::QX : H::QX * H::QY);
+      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[-e] - (R)qa[e]) * (R)0.5;
+    }
+  } else {
+    const A* a_q = (const A*)d.aux + 2 * d.PN;
+    const long long pc = pnode_of<D>(d, x, y, z);
+    const long long sy = d.px, sz = (long long)d.px * d.py;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const A* qa = a_q + a * d.PN;
+      const long long e = a == 0 ? 1 : (a == 1 ? sy : sz);
+      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc - e] - (R)qa[pc + e]) * (R)0.5;
+    }
+  }
+  if (kStaged) {
+    // the block is done with the staged fields (a block-wide vote on the copy's arrival)
+    if (__syncthreads_or(!tile_ok)) {
+      if (tid == 0) atomicOr(d.flags, 2u);
+      mbar_wait_bounded(bar, phase, kTileWaitPolls);
+      return false;
+    }
+    hooks.aux();
+    if (!active) return true;
+  }
+
+  collide_relax<D, R, NT>(d, ph, n, m, inv_rho, u, F, Phi, om, fp, fs, s_h, tid);
 
   // ---- float16-deviation storage: encode against this node's density, which the
   //      next step reads back as the writer density of every slot written here

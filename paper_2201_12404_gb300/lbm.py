@@ -26,6 +26,10 @@ LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
 LBM_GAMMA_ENTROPIC, LBM_GAMMA_FIXED = 0, 1
 
+# Device allocator hooks of lbm_params: void* (*)(size_t, void*) and void (*)(void*, void*).
+DEV_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEV_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
                 4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -46,6 +50,7 @@ class lbm_params(ctypes.Structure):
         ("gamma_mode", ctypes.c_int32), ("gamma_value", ctypes.c_double),
         ("eos_fp64", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("alloc_ctx", ctypes.c_void_p),
     ]
 
 
@@ -137,6 +142,31 @@ def lbm_default_params(**overrides) -> lbm_params:
                 arr[i] = x
         else:
             setattr(p, k, v)
+    return p
+
+
+def _torch_alloc(nbytes, ctx):
+    import torch
+    try:
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+    except Exception:  # out of memory: the library reports LBM_ERR_OOM
+        return None
+
+
+def _torch_free(ptr, ctx):
+    import torch
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+# module-level so that the C function pointers stay valid for every domain's lifetime
+_TORCH_HOOKS = (DEV_ALLOC(_torch_alloc), DEV_FREE(_torch_free))
+
+
+def use_torch_allocator(p: lbm_params) -> lbm_params:
+    """Route the device buffers of domains created from p through PyTorch's caching
+    allocator (torch.cuda.caching_allocator_alloc/delete) on the current device."""
+    p.dev_alloc, p.dev_free = _TORCH_HOOKS
+    p.alloc_ctx = None
     return p
 
 

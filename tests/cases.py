@@ -68,3 +68,66 @@ def rel_err(f_gpu, f_orc, D):
     w = O.weights(D).reshape((-1, 1, 1, 1))
     rho = f_orc.sum(axis=0, keepdims=True)
     return np.abs(f_gpu - f_orc) / (w * rho)
+
+
+def fp32_step_check(f_s, fg, fo, po, gamma_gpu, tol=2e-6, sample=None, seed=3):
+    """Check one float32 GPU step fg against the oracle's fo from the same state f_s.
+
+    Float32 resolves a population only to ~6e-8 of w_i rho.  Near equilibrium the
+    higher-order part h = f - f^eq - s falls to ~1e-5 of w_i rho, so the entropic
+    sums <ds|dh>, <dh|dh> built from it, and the gamma they give (Sec. 2.4), are
+    float32 noise there; gamma multiplies h in the relaxation, so the population
+    error that noise causes is (omega/2) |gamma_gpu - gamma_orc| |h| (reading A-9:
+    no clipping, gamma noise is harmless where h is small).  Every population must
+    therefore lie within tol w_i rho plus that term of the node it was streamed
+    from (measured gamma_gpu, oracle gamma, omega and h), and where h is
+    resolvable (max |h_i|/(w_i rho) >= 1e-3) gamma itself must agree to 2e-3.
+    `sample` limits the conditioning check to that many seeded nodes.
+    Returns (worst error over allowed bound, plain max error, nodes checked)."""
+    D = po.D
+    Q = O.Q_of(D)
+    c = O.velocities(D)
+    w = O.weights(D)
+    e = rel_err(fg, fo, D)
+    rho_d = fo.sum(axis=0)
+    rho, u, spsi, q = O.aux_fields(po, f_s)
+    F = O.force(po, rho, spsi)
+    Phi = O.phi(po, rho, q)
+    cache = {}
+    dims = [po.nx, po.ny, po.nz if D == 3 else 1]
+
+    def node(z, y, x):
+        key = (z, y, x)
+        if key not in cache:
+            f = f_s[:, z, y, x]
+            om = O.omega(po, f.sum())
+            res = O.collide_node(D, f, F[:, z, y, x], Phi[:, z, y, x], om)
+            cache[key] = (res["h"], res["gamma"], om)
+        return cache[key]
+
+    worst = 0.0
+    for i, z, y, x in np.argwhere(e > tol):
+        src = [x - c[i, 0], y - c[i, 1], z - c[i, 2]]
+        j = i
+        for a in range(D):
+            if src[a] < 0 or src[a] >= dims[a]:
+                if po.bc[2 * a + (0 if src[a] < 0 else 1)] == 1:  # bounce-back: the node itself, reversed
+                    src, j = [x, y, z], Q - 1 - i
+                    break
+                src[a] %= dims[a]
+        sx, sy, sz = src
+        h, g_orc, om = node(sz, sy, sx)
+        allowed = tol * w[i] * rho_d[z, y, x] + 1.05 * 0.5 * om * abs(gamma_gpu[sz, sy, sx] - g_orc) * abs(h[j])
+        worst = max(worst, abs(fg[i, z, y, x] - fo[i, z, y, x]) / allowed)
+    # gamma where the entropic sums are resolvable
+    shape = f_s.shape[1:]
+    nodes = [(z, y, x) for z in range(shape[0]) for y in range(shape[1]) for x in range(shape[2])]
+    if sample is not None and sample < len(nodes):
+        pick = np.random.default_rng(seed).choice(len(nodes), sample, replace=False)
+        nodes = [nodes[k] for k in pick]
+    for z, y, x in nodes:
+        h, g_orc, om = node(z, y, x)
+        r = f_s[:, z, y, x].sum()
+        if np.max(np.abs(h) / (w * r)) >= 1e-3:
+            assert abs(gamma_gpu[z, y, x] - g_orc) <= 2e-3, ((z, y, x), gamma_gpu[z, y, x], g_orc)
+    return worst, e.max(), len(nodes)

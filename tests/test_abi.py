@@ -51,9 +51,10 @@ def test_params_struct_layout_matches_header(L):
 #include <stdio.h>
 #include "lbm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, a),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, a),
          offsetof(lbm_params, body_force), offsetof(lbm_params, bc), offsetof(lbm_params, gamma_value),
-         offsetof(lbm_params, eos_fp64), offsetof(lbm_params, stream));
+         offsetof(lbm_params, eos_fp64), offsetof(lbm_params, stream), offsetof(lbm_params, dev_alloc),
+         offsetof(lbm_params, dev_free), offsetof(lbm_params, alloc_ctx));
   return 0;
 }
 '''
@@ -66,7 +67,8 @@ int main(void) {
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     P = lbm.lbm_params
     assert vals == [ctypes.sizeof(P), P.a.offset, P.body_force.offset, P.bc.offset, P.gamma_value.offset,
-                    P.eos_fp64.offset, P.stream.offset]
+                    P.eos_fp64.offset, P.stream.offset, P.dev_alloc.offset, P.dev_free.offset,
+                    P.alloc_ctx.offset]
 
 
 def test_default_params_and_footprint(L):
