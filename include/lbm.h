@@ -339,22 +339,36 @@ const char* lbm_version(void);
  *   nsteps       even and >= 0, so that the state is in canonical order again on
  *                return.
  *
- * The auxiliary fields between the two passes live in a 16 MiB scratch array
+ * The auxiliary fields between the passes live in a 16 MiB scratch array
  * compiled into the library (every GPU that loads the library holds it until
- * the process exits).  Domains whose (2 + D) padded auxiliary fields,
- * px(ny+4)(nz+4) values each in the storage type with px = nx+4 rounded up to
- * a multiple of 4, need more than 16 MiB - 256 B are rejected: for example
- * 64x64x128 D3Q27 in float32 fits, 128^3 does not; 1000x1000 D2Q9 in float32
- * fits.
+ * the process exits).  Domains whose 2 + 2D padded auxiliary fields, ((rho,
+ * psi) pairs, q and j), px(ny+4)(nz+4) values each in the storage type with
+ * px = nx+4 rounded up to a multiple of 4, need more than 16 MiB - 256 B are
+ * rejected: for example 64x64x96 D3Q27 in float32 fits, 64x64x128 does not;
+ * 800x800 D2Q9 in float32 fits, 1000x1000 does not.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  Every call shares the one array: calls that overlap on
  * the GPU (two streams, or two host threads) race and corrupt each other.
- * Asynchronous: returns once the work is enqueued.  No instability check.
+ * Asynchronous: returns once the work is enqueued.  Instabilities (a
+ * non-finite or non-positive density) and bounded device waits that gave up
+ * are not reported here: read them with lbm_noalloc_status once the stream's
+ * work has completed.
  * Returns LBM_ERR_INVALID_ARG for NULL pointers, invalid parameters, LBM_FP16DEV,
- * odd or negative nsteps, or a domain beyond the scratch maximum; LBM_ERR_CUDA if the
+ * odd or negative nsteps, populations not aligned to their storage type, or a
+ * domain beyond the scratch maximum; LBM_ERR_CUDA if a CUDA error was already
+ * pending when the call began (it is left pending for the caller) or if the
  * symbol lookup or a launch fails. */
 lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, int64_t nsteps);
+
+/* Outcome of the last lbm_step_noalloc call on the current device, for the same
+ * callers (the paper has no counterpart): LBM_ERR_TIMEOUT if one of its bounded
+ * device-side waits gave up (those tiles were left unwritten), else
+ * LBM_ERR_UNSTABLE if a non-finite or non-positive density appeared, else LBM_OK;
+ * LBM_ERR_CUDA if the flag word cannot be read.  Reads the flag word at the start
+ * of the shared scratch array into a host variable (no allocation); call it after
+ * the stream that ran the steps has completed, before the next call clears it. */
+lbm_status lbm_noalloc_status(void);
 
 #ifdef __cplusplus
 }

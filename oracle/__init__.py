@@ -101,7 +101,8 @@ def load_library(path: str):
                                             ctypes.c_int, ctypes.c_double, _dp,
                                             ctypes.POINTER(ctypes.c_double),
                                             _dp, _dp, _dp, _dp, _dp]),
-        "orc_aux_fields": (None, [P, _dp, _dp, _dp, _dp, _dp]),
+        "orc_aux_fields": (None, [P, _dp, _dp, _dp, _dp]),
+        "orc_qflux": (None, [P, _dp, _dp, _dp, _dp]),
         "orc_force": (None, [P, _dp, _dp, _dp]),
         "orc_phi": (None, [P, _dp, _dp, _dp]),
         "orc_init_equilibrium": (None, [P, _dp, _dp, _dp]),
@@ -237,14 +238,21 @@ def collide_node(D, f, F, Phi, omega_, gamma_mode=0, gamma_value=2.0):
 # ---- fields ---------------------------------------------------------------------------
 
 def aux_fields(p: Params, f):
+    """(rho, bare u, s psi) of a state."""
     D = p.D
     sh = _shape(p)
     rho = np.zeros(sh)
     u = np.zeros((D,) + sh)
     spsi = np.zeros(sh)
-    q = np.zeros((D,) + sh)
-    lib().orc_aux_fields(ctypes.byref(p), _f64(f), rho, u, spsi, q)
-    return rho, u, spsi, q
+    lib().orc_aux_fields(ctypes.byref(p), _f64(f), rho, u, spsi)
+    return rho, u, spsi
+
+
+def qflux(p: Params, rho, u, F):
+    """q_a = rho v_a^3, v = u + F/(2 rho), the flux Phi differentiates."""
+    q = np.zeros((p.D,) + _shape(p))
+    lib().orc_qflux(ctypes.byref(p), _f64(rho), _f64(u), _f64(F), q)
+    return q
 
 
 def force(p: Params, rho, spsi):

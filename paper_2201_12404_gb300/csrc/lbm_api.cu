@@ -25,8 +25,6 @@ namespace {
 
 const char* kVersion = "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP32/FP16-deviation, A-A streaming, sm_103a";
 
-bool is_wall(int v) { return v == LBM_BC_BOUNCEBACK; }
-
 using lbm::EosCoeffs;
 using lbm::eos_coeffs;
 using lbm::pr_p;
@@ -73,7 +71,7 @@ Sizes sizes_of(const lbm_params& p, const Ops* ops) {
   s.pz = s.D == 3 ? p.nz + 4 : 1;
   s.PN = (long long)s.px * s.py * s.pz;
   s.f_bytes = (size_t)s.Q * s.N * ops->pop_bytes;
-  s.aux_bytes = (size_t)(2 + s.D) * s.PN * ops->aux_bytes;
+  s.aux_bytes = (size_t)lbm::aux_fields_per_node(s.D) * s.PN * ops->aux_bytes;
   s.gamma_bytes = (size_t)s.N * sizeof(float);
   s.rho_w_bytes = p.precision == LBM_FP16DEV ? 2 * (size_t)s.N * sizeof(float) : 0;
   return s;
@@ -225,8 +223,14 @@ lbm_status launch_k(lbm_domain* h, int kind) {
     b = take_event(h);
     LBM_CUDA(h, cudaEventRecord(a, h->stream));
   }
-  if (kind == 0) h->ops->moments_eos(h->dev, h->parity, h->stream);
-  else h->ops->collide_stream(h->dev, h->maps, h->parity, h->stream);
+  if (kind == 0) {
+    // pass 1 and the q planes it feeds, timed together
+    h->ops->moments_eos(h->dev, h->parity, h->stream);
+    h->ops->qflux(h->dev, h->maps, h->stream);
+    h->launches += 2;
+  } else {
+    h->ops->collide_stream(h->dev, h->maps, h->parity, h->stream);
+  }
   h->launches += 1;
   LBM_CUDA(h, cudaGetLastError());
   if (h->timing) {
@@ -407,16 +411,8 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out) {
   h->ops = ops_for(*p);
   const Sizes s = sizes_of(*p, h->ops);
   DevDomain& d = h->dev;
-  d.N = s.N; d.PN = s.PN;
-  d.nx = p->nx; d.ny = p->ny; d.nz = s.D == 3 ? p->nz : 1;
-  d.px = s.px; d.py = s.py; d.pz = s.pz;
-  for (int a = 0; a < 3; ++a) {
-    const bool active = a < s.D;
-    d.wall_lo[a] = active && is_wall(p->bc[2 * a]);
-    d.wall_hi[a] = active && is_wall(p->bc[2 * a + 1]);
-  }
+  lbm::fill_geometry(d, *p, s.D, h->ops->pop_bytes);
   lbm::fill_phys(d, *p, s.D);
-  lbm::fill_slot_offsets(d, s.D, h->ops->pop_bytes);
 
   auto bail = [&](cudaError_t err, const char* where) {
     g_create_error = std::string(where) + ": " + cudaGetErrorString(err);

@@ -292,7 +292,7 @@ lbm_status lbm_batch_tune(lbm_batch_handle b, int32_t trial_steps, const char* c
     const lbm_domain* h = b->doms[j];
     DevDomain c = h->dev;
     const size_t fb = (size_t)h->ops->Q * h->dev.N * h->ops->pop_bytes;
-    const size_t ab = (size_t)(2 + h->ops->D) * h->dev.PN * h->ops->aux_bytes;
+    const size_t ab = (size_t)(2 + 2 * h->ops->D) * h->dev.PN * h->ops->aux_bytes;
     void *f = nullptr, *aux = nullptr, *fl = nullptr, *rw = nullptr;
     if (cudaMalloc(&f, fb) != cudaSuccess || cudaMalloc(&aux, ab) != cudaSuccess || cudaMalloc(&fl, 64) != cudaSuccess) {
       if (f) cudaFree(f);

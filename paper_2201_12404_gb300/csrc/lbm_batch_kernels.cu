@@ -66,6 +66,18 @@ __global__ void __launch_bounds__(BX * BY, sizeof(R) == 4 ? LBM_BATCH_MINBLOCKS_
       else moments_eos_node<2, 1, S, R, A>(d, xp, yp, 0);
     }
     if (!grid_barrier(a.barrier, a.error)) return;
+    // pass 1b: q over the interior tiles, then its ghost layers over the padded tiles
+    for (int it = blockIdx.x; it < a.n_k2; it += gridDim.x) {
+      __syncthreads();  // the previous tile's threads are done with s_aux
+      const BatchItem w = a.k2[it];
+      qflux_tile<2, BX, BY, 1, R, A, false>(a.jobs[w.job], nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, 0);
+    }
+    if (!grid_barrier(a.barrier, a.error)) return;
+    for (int it = blockIdx.x; it < a.n_k1; it += gridDim.x) {
+      const BatchItem w = a.k1[it];
+      qflux_ghost_node<2, A>(a.jobs[w.job], w.tx * BX + threadIdx.x, w.ty * BY + threadIdx.y, 0);
+    }
+    if (!grid_barrier(a.barrier, a.error)) return;
     for (int it = blockIdx.x; it < a.n_k2; it += gridDim.x) {
       __syncthreads();  // the previous tile's threads are done with s_aux and s_h
       const BatchItem w = a.k2[it];

@@ -638,6 +638,77 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   return true;
 }
 
+// Pass 1b on one tile of interior nodes whose origin is (x0, y0, z0): q_a = rho v_a^3
+// (Eq. (correction) with P0/rho = cs^2) at every node of the tile, with v = (j +
+// F/2)/rho the fluid velocity of the exact-difference forcing and F the force of
+// Eq. (Kforce_final) from the staged (rho, psi) halo tile (the stencil of pass 2),
+// j and rho those pass 1 wrote for the node.  kTma: the halo tile comes from one
+// TMA copy on `bar` (phase `phase`); otherwise each warp loads halo rows.  The
+// ghost layers of q are filled afterwards from their images.  Returns false when
+// the halo copy did not arrive within the poll limit.
+template <int D, int BX, int BY, int BZ, typename R, typename A, bool kTma>
+__device__ __forceinline__ bool qflux_tile(const DevDomain& d, const TileMaps* maps, int x0, int y0, int z0,
+                                           Two<A>* s_aux, unsigned long long* bar, uint32_t phase) {
+  constexpr int NT = BX * BY * BZ;
+  using H = Halo<D, BX, BY, BZ>;
+  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+  if (kTma) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)(H::HN * sizeof(Two<A>)));
+      tma_load_tile<D, A>(s_aux, &maps->aux, bar, x0, y0, z0);
+    }
+  } else {
+    const Two<A>* a2 = (const Two<A>*)d.aux;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < H::HY * H::HZ; r += NT / 32) {
+      const int yp = y0 + r % H::HY, zp = z0 + r / H::HY;
+      const bool row_ok = yp < d.py && zp < d.pz;
+      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
+      for (int hx = lane; hx < H::HX; hx += 32) {
+        const bool ok = row_ok && x0 + hx < d.px;
+        s_aux[r * H::HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
+      }
+    }
+    __syncthreads();
+  }
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
+  const bool active = x < d.nx && y < d.ny && z < d.nz;
+  if (kTma && !mbar_wait_bounded(bar, phase, kTileWaitPolls)) {
+    // every thread waits, so that the block cannot retire while the copy is in flight
+    if (tid == 0) atomicOr(d.flags, 2u);
+    mbar_wait_bounded(bar, phase, kTileWaitPolls);
+    return false;
+  }
+  if (!active) return true;
+  const int sc = (threadIdx.x + 2) + H::HX * ((threadIdx.y + 2) + H::HY * (D == 3 ? threadIdx.z + 2 : 0));
+  const R rho = (R)s_aux[sc].x;
+  R F[3];
+  stencil_force<D, R, A>(phys<R>(d), rho, [&](int dx, int dy, int dz) { return s_aux[sc + dx + H::HX * (dy + H::HY * dz)]; },
+                         F);
+  A* aux = (A*)d.aux;
+  const long long pn = pnode_of<D>(d, x, y, z);
+  const R inv = (R)1 / rho;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const R v = ((R)aux[(2 + D + a) * d.PN + pn] + (R)0.5 * F[a]) * inv;
+    aux[(2 + a) * d.PN + pn] = (A)(rho * v * v * v);
+  }
+  return true;
+}
+
+template <int D, typename R, typename A>
+__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz)
+qflux_tile_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
+  constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
+  using H = Halo<D, BX, BY, BZ>;
+  __shared__ __align__(128) Two<A> s_aux[H::HN];
+  __shared__ __align__(8) unsigned long long tile_bar;
+  if (threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z) == 0) mbar_init(&tile_bar, 1);
+  __syncthreads();
+  qflux_tile<D, BX, BY, BZ, R, A, true>(d, &maps, blockIdx.x * BX, blockIdx.y * BY, D == 3 ? blockIdx.z * BZ : 0,
+                                         s_aux, &tile_bar, 0);
+}
+
 template <int D, int P, typename S, typename R, typename A>
 __global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R, D))
 collide_stream_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {

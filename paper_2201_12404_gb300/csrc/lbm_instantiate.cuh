@@ -19,6 +19,12 @@ struct Launch {
     if (parity == 0) moments_eos_kernel<D, 0, S, R, A><<<grd, blk, 0, s>>>(d);
     else moments_eos_kernel<D, 1, S, R, A><<<grd, blk, 0, s>>>(d);
   }
+  static void qflux(const DevDomain& d, const TileMaps& maps, cudaStream_t s) {
+    dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
+    qflux_tile_kernel<D, R, A><<<node_grid(d), blk, 0, s>>>(d, maps);
+    dim3 grd((d.px + blk.x - 1) / blk.x, (d.py + blk.y - 1) / blk.y, (d.pz + blk.z - 1) / blk.z);
+    qflux_ghost_kernel<D, A><<<grd, blk, 0, s>>>(d);
+  }
   static void collide_stream(const DevDomain& d, const TileMaps& maps, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
     if constexpr (sizeof(S) == 8) {
@@ -121,7 +127,7 @@ struct Launch {
     return (int)nb;
   }
   static Ops table() {
-    return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &collide_stream, &init_equilibrium, &aux_density,
+    return Ops{D, Lattice<D>::Q, sizeof(S), sizeof(A), &moments_eos, &qflux, &collide_stream, &init_equilibrium, &aux_density,
                &canonical_read, &canonical_write, &canonical_window, &macroscopic, &bare_velocity, &diag_partial,
                &max_speed_partial, &drop_on_film, &grad_partial, &crown_partial};
   }

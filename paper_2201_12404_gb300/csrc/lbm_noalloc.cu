@@ -4,11 +4,12 @@
 // framework that owns the whole device memory pool, a memory-capped process,
 // or a host thread that must not touch the allocator while other work is in
 // flight.  They hand in the populations they own; the auxiliary fields that the
-// step needs between its two passes (density, signed pseudo-potential, q) live
+// step needs between its passes (density, signed pseudo-potential, q, j) live
 // in a fixed scratch array compiled into this library instead of a cudaMalloc.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/lbm.h"
@@ -56,21 +57,17 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   const int D = p->lattice == LBM_D3Q27 ? 3 : 2;
   const Ops* ops = p->lattice == LBM_D2Q9 ? (p->precision == LBM_FP64 ? &lbm::ops_d2q9_fp64 : &lbm::ops_d2q9_fp32)
                                           : (p->precision == LBM_FP64 ? &lbm::ops_d3q27_fp64 : &lbm::ops_d3q27_fp32);
+  // every population access is one aligned word of the storage type
+  if ((uintptr_t)populations % ops->pop_bytes != 0) return LBM_ERR_INVALID_ARG;
   DevDomain d{};
-  d.N = (long long)p->nx * p->ny * (D == 3 ? p->nz : 1);
-  d.nx = p->nx; d.ny = p->ny; d.nz = D == 3 ? p->nz : 1;
-  d.px = lbm::padded_x(p->nx); d.py = p->ny + 4; d.pz = D == 3 ? p->nz + 4 : 1;
-  d.PN = (long long)d.px * d.py * d.pz;
-  const double aux_bytes = (double)(2 + D) * (double)d.PN * (double)ops->aux_bytes;
+  lbm::fill_geometry(d, *p, D, ops->pop_bytes);
+  const double aux_bytes = (double)lbm::aux_fields_per_node(D) * (double)d.PN * (double)ops->aux_bytes;
   if (aux_bytes > (double)(kScratchBytes - kHeaderBytes)) return LBM_ERR_INVALID_ARG;  // beyond the scratch maximum
   if (nsteps == 0) return LBM_OK;
-
-  for (int a = 0; a < 3; ++a) {
-    d.wall_lo[a] = a < D && p->bc[2 * a] == LBM_BC_BOUNCEBACK;
-    d.wall_hi[a] = a < D && p->bc[2 * a + 1] == LBM_BC_BOUNCEBACK;
-  }
+  // an error the caller left pending is theirs: report it without doing any work
+  // (and without clearing it)
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ERR_CUDA;
   lbm::fill_phys(d, *p, D);
-  lbm::fill_slot_offsets(d, D, ops->pop_bytes);
 
   unsigned char* scratch = nullptr;
   lbm_status st = scratch_address(&scratch);
@@ -91,8 +88,22 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, i
   int parity = 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     ops->moments_eos(d, parity, stream);
+    ops->qflux(d, maps, stream);
     ops->collide_stream(d, maps, parity, stream);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     parity ^= 1;
   }
-  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_noalloc_status(void) {
+  unsigned char* scratch = nullptr;
+  lbm_status st = scratch_address(&scratch);
+  if (st != LBM_OK) return st;
+  unsigned int flags = 0;
+  // a pageable host word: the copy allocates nothing
+  if (cudaMemcpy(&flags, scratch, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ERR_CUDA;
+  if (flags & 2u) return LBM_ERR_TIMEOUT;
+  if (flags & 1u) return LBM_ERR_UNSTABLE;
+  return LBM_OK;
 }

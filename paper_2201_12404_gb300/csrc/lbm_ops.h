@@ -14,6 +14,8 @@ struct Ops {
   size_t pop_bytes;  // bytes per stored population
   size_t aux_bytes;  // bytes per auxiliary value
   void (*moments_eos)(const DevDomain&, int parity, cudaStream_t);
+  // q planes, ghosts included, from the (rho, psi) pairs and j planes pass 1 wrote
+  void (*qflux)(const DevDomain&, const TileMaps& maps, cudaStream_t);
   void (*collide_stream)(const DevDomain&, const TileMaps& maps, int parity, cudaStream_t);
   void (*init_equilibrium)(const DevDomain&, const double* rho, const double* ux, const double* uy,
                            const double* uz, cudaStream_t);
@@ -162,6 +164,25 @@ inline bool make_q_map(CUtensorMap* map, const DevDomain& d, int D, size_t elem_
     return false;
   }
   return true;
+}
+
+// Auxiliary values per padded node: the (rho, psi) pair, the D q planes and the D
+// j planes.
+inline int aux_fields_per_node(int D) { return 2 + 2 * D; }
+
+// Extents, walls and slot offsets of the domain p describes, with populations
+// stored in pop_bytes bytes (the physical parameters come from fill_phys).
+// Shared by lbm_create_domain and lbm_step_noalloc.
+inline void fill_geometry(DevDomain& d, const lbm_params& p, int D, size_t pop_bytes) {
+  d.nx = p.nx; d.ny = p.ny; d.nz = D == 3 ? p.nz : 1;
+  d.N = (long long)d.nx * d.ny * d.nz;
+  d.px = padded_x(p.nx); d.py = p.ny + 4; d.pz = D == 3 ? p.nz + 4 : 1;
+  d.PN = (long long)d.px * d.py * d.pz;
+  for (int a = 0; a < 3; ++a) {
+    d.wall_lo[a] = a < D && p.bc[2 * a] == LBM_BC_BOUNCEBACK;
+    d.wall_hi[a] = a < D && p.bc[2 * a + 1] == LBM_BC_BOUNCEBACK;
+  }
+  fill_slot_offsets(d, D, pop_bytes);
 }
 
 inline bool make_tile_maps(TileMaps* m, const DevDomain& d, int D, size_t elem_bytes, const char** why) {

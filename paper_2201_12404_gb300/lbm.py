@@ -106,6 +106,7 @@ def load():
                 "lbm_last_error": (ctypes.c_char_p, [H]),
                 "lbm_version": (ctypes.c_char_p, []),
                 "lbm_step_noalloc": (st, [P, ctypes.c_void_p, ctypes.c_int64]),
+                "lbm_noalloc_status": (st, []),
                 "lbm_batch_create": (st, [ctypes.POINTER(H), ctypes.c_int32, ctypes.POINTER(H)]),
                 "lbm_batch_step": (st, [H, ctypes.c_int64]),
                 "lbm_batch_synchronize": (st, [H]),
@@ -196,8 +197,13 @@ def lbm_step_noalloc(p: lbm_params, populations_ptr: int, nsteps: int) -> None:
     """Allocation-free stepping of caller-owned device populations (see include/lbm.h)."""
     st = load().lbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(populations_ptr), int(nsteps))
     if st != LBM_OK:
-        raise LBMError(st, "lbm_step_noalloc failed (invalid parameters, odd nsteps, a domain beyond "
-                           "the 16 MiB scratch, or a CUDA error)")
+        raise LBMError(st, "lbm_step_noalloc failed (invalid parameters, odd nsteps, misaligned populations, "
+                           "a domain beyond the 16 MiB scratch, or a CUDA error)")
+
+
+def lbm_noalloc_status() -> int:
+    """Status of the last lbm_step_noalloc on the current device (after its stream completed)."""
+    return int(load().lbm_noalloc_status())
 
 
 class lbm_drop_on_film(ctypes.Structure):

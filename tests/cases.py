@@ -90,9 +90,9 @@ def fp32_step_check(f_s, fg, fo, po, gamma_gpu, tol=2e-6, sample=None, seed=3):
     w = O.weights(D)
     e = rel_err(fg, fo, D)
     rho_d = fo.sum(axis=0)
-    rho, u, spsi, q = O.aux_fields(po, f_s)
+    rho, u, spsi = O.aux_fields(po, f_s)
     F = O.force(po, rho, spsi)
-    Phi = O.phi(po, rho, q)
+    Phi = O.phi(po, rho, O.qflux(po, rho, u, F))
     cache = {}
     dims = [po.nx, po.ny, po.nz if D == 3 else 1]
 

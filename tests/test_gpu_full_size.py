@@ -5,8 +5,9 @@ on the vertical axis, periodic elsewhere) are stepped on the GPU exactly as the
 benchmark steps them: the same parameters, the same seeded initial fields through
 lbm_init_fields, the same grid and kernels, on a dedicated stream.  The oracle
 cannot step 67M nodes in a test, but one node after K steps depends only on the
-initial fields within a radius of 3K + 2 (Sec. 2: the force reaches two nodes,
-streaming one more; the initial velocity shift F/(2 rho) reaches two).  So for
+initial fields within a radius of 4K + 2 (Sec. 2: the force reaches two nodes,
+Phi one more through the force in its q, streaming one more; the initial
+velocity shift F/(2 rho) reaches two).  So for
 each sample node the oracle runs K steps on a window of the initial fields with
 that margin around the nodes it checks, and those nodes are compared with the
 GPU's state read back through lbm_read_populations_window.

@@ -50,7 +50,11 @@ MUTANTS = [
      [("test_diagonal_correction_makes_sound_damping_galilean_invariant", {"D": 2})]),
     ("q not negated across a wall", "double qp = q[al * N + np_] * (flp ? -1.0 : 1.0);", "double qp = q[al * N + np_];",
      [("test_walls_equal_the_mirrored_periodic_domain", {"D": 2})]),
-    ("q = rho u^2", "q[al * N + n] = r * ua * (ua * ua + 3.0 * CS2 - 3.0 * CS2);", "q[al * N + n] = r * ua * ua;",
+    ("q from the bare velocity", "double v = u[al * N + n] + F[al * N + n] / (2.0 * rho[n]);", "double v = u[al * N + n];",
+     [("test_phi_vanishes_for_a_fluid_at_rest", {"D": 2})]),
+    ("q with the whole force", "double v = u[al * N + n] + F[al * N + n] / (2.0 * rho[n]);",
+     "double v = u[al * N + n] + F[al * N + n] / rho[n];", [("test_phi_vanishes_for_a_fluid_at_rest", {"D": 2})]),
+    ("q = rho u^2", "q[al * N + n] = rho[n] * v * (v * v + 3.0 * CS2 - 3.0 * CS2);", "q[al * N + n] = rho[n] * v * v;",
      [("test_diagonal_correction_makes_sound_damping_galilean_invariant", {"D": 2})]),
     ("equilibrium zeta without u^2", "zeta[al] = CS2 + u[al] * u[al]; }", "zeta[al] = CS2; }",
      [("test_feq_central_moments_vanish", {"D": 2})]),

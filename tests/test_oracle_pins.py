@@ -361,6 +361,35 @@ def test_phi_central_difference():
         assert np.max(np.abs(Phi[a] - ex)) / np.max(np.abs(ex)) < 2.5e-3
 
 
+@pytest.mark.parametrize("D", [2, 3])
+def test_phi_vanishes_for_a_fluid_at_rest(D):
+    """Phi corrects a Galilean defect of the lattice's third moment (Sec. 2.2), so it
+    vanishes for a fluid at rest.  A drop at rest in the reported sense (f = f^eq at
+    the bare velocity -F/(2 rho), whose fluid velocity u + F/(2 rho) is zero) has
+    q = 0 and Phi = 0 to round-off; the bare velocity alone would leave Phi at every
+    interface.  For a uniform flow without force q is rho u^3 (the Galilean case the
+    sound-damping pin covers)."""
+    n = 16 if D == 2 else 10
+    p, _ = _two_phase_drop(D, n)
+    shape = (n if D == 3 else 1, n, n)
+    rho0 = I.drop(shape, (n / 2, n / 2, n / 2), n / 4, p.rho_liquid, p.rho_vapour, 4.0, D=D)
+    f = O.init_physical(p, rho0, np.zeros((D,) + shape))
+    rho, u, spsi = O.aux_fields(p, f)
+    F = O.force(p, rho, spsi)
+    q = O.qflux(p, rho, u, F)
+    Phi = O.phi(p, rho, q)
+    bare = O.phi(p, rho, rho * u ** 3)
+    assert np.max(np.abs(bare)) > 1e-9
+    assert np.max(np.abs(Phi)) < 1e-17
+    # uniform flow, no force: q = rho u^3 (to 1e-12: the oracle evaluates the printed
+    # bracket u^2 + 3 P0/rho - 3 cs^2, adding and removing 1)
+    U = np.array([0.05, -0.03, 0.02])[:D].reshape((D,) + (1,) * 3)
+    r1 = np.full(shape, 1.3)
+    u1 = np.broadcast_to(U, (D,) + shape).copy()
+    q1 = O.qflux(p, r1, u1, np.zeros((D,) + shape))
+    assert np.allclose(q1, r1 * u1 ** 3, rtol=1e-12, atol=0)
+
+
 # ---- Sec. 3.1: equation of state and Maxwell construction ---------------------------------
 
 def test_oracle_pressure_matches_thermo():

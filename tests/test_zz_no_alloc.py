@@ -2,11 +2,13 @@
 device allocation (for callers that cannot allocate: a framework that owns the
 whole memory pool, a memory-capped process).  Its output must match the
 handle-based lbm_step on the same state, call after call, within the parity
-tolerances of the GPU tests.  This file is collected last on purpose."""
+tolerances of the GPU tests, and the FP64 oracle within the same per-step bounds.
+This file is collected last on purpose."""
 import numpy as np
 import pytest
 
-from cases import case, drop_state, lbm_params
+import oracle as O
+from cases import case, drop_state, lbm_params, oracle_params
 from paper_2201_12404_gb300 import lbm
 
 pytestmark = pytest.mark.gpu
@@ -49,10 +51,14 @@ def test_noalloc_matches_lbm_step_on_two_calls(D, dims, precision):
             ref = dom.lbm_read_populations()
             lbm.lbm_step_noalloc(p, dev.data_ptr(), 2)
             torch.cuda.synchronize()
+            assert lbm.lbm_noalloc_status() == lbm.LBM_OK
             got = dev.double().cpu().numpy()
             assert np.isfinite(got).all()
             err = _scaled_diff(got, ref, D)
             assert err <= TOL[precision], (call, err)
+    # both calls together against the oracle: four steps
+    fo, _ = O.run(oracle_params(c), f0, 4)
+    assert _scaled_diff(got, fo, D) <= 4 * TOL[precision]
 
 
 def test_noalloc_rejects_beyond_scratch_and_odd_steps():
@@ -68,3 +74,29 @@ def test_noalloc_rejects_beyond_scratch_and_odd_steps():
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_step_noalloc(small, dummy.data_ptr(), 3)
     assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    # populations that do not start on a float32 boundary are refused before any launch
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_step_noalloc(small, dummy.data_ptr() + 2, 2)
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_noalloc_status_reports_an_instability():
+    """A non-finite population makes the density non-finite: the steps complete and
+    lbm_noalloc_status reports LBM_ERR_UNSTABLE; a clean state afterwards reads OK
+    again (each call clears the flag word)."""
+    import torch
+    torch.cuda.set_device(0)
+    c = case(2, 32, 20, precision=lbm.LBM_FP64)
+    p = lbm_params(c)
+    p.stream = torch.cuda.current_stream().cuda_stream
+    f0 = drop_state(c)
+    bad = f0.copy()
+    bad[4, 0, 7, 9] = np.nan
+    dev = torch.from_numpy(bad).cuda().contiguous()
+    lbm.lbm_step_noalloc(p, dev.data_ptr(), 2)
+    torch.cuda.synchronize()
+    assert lbm.lbm_noalloc_status() == lbm.LBM_ERR_UNSTABLE
+    dev = torch.from_numpy(f0).cuda().contiguous()
+    lbm.lbm_step_noalloc(p, dev.data_ptr(), 2)
+    torch.cuda.synchronize()
+    assert lbm.lbm_noalloc_status() == lbm.LBM_OK

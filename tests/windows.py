@@ -1,9 +1,10 @@
 """Windows of a large domain that the oracle can step exactly.
 
 One node after K steps from lbm_init_fields depends only on the initial fields
-within a radius of 3K + 2: the force reaches two nodes (Sec. 2, the stencils of
-the pseudo-potential and of the Korteweg term), streaming one more per step, and
-the initial velocity shift F/(2 rho) two.  A window with that margin around the
+within a radius of 4K + 2: the force reaches two nodes (Sec. 2, the stencils of
+the pseudo-potential and of the Korteweg term), Phi one more (its q is formed
+with the force of the neighbouring nodes), streaming one more per step, and the
+initial velocity shift F/(2 rho) two.  A window with that margin around the
 nodes it checks therefore gives those nodes exactly, whatever the window's own
 faces do.  Windows wrap across periodic faces; along a wall axis they are clipped
 to the domain and a face that is not a true wall gets a bounce-back wall.
@@ -15,7 +16,7 @@ from paper_2201_12404_gb300 import inputs as I
 from paper_2201_12404_gb300 import workloads as WL
 
 K = 4                    # steps: even, odd, even, odd A-A parities
-MARGIN = 3 * K + 2       # dependency radius of a node after K steps from lbm_init_fields
+MARGIN = 4 * K + 2       # dependency radius of a node after K steps from lbm_init_fields
 VALID = 4                # checked nodes per axis in a periodic window
 
 
