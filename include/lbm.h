@@ -308,6 +308,15 @@ lbm_status lbm_batch_synchronize(lbm_batch_handle b);
  * count) is used without timing, and a new choice is appended.  Synchronising. */
 lbm_status lbm_batch_tune(lbm_batch_handle b, int32_t trial_steps, const char* cache_path);
 
+/* Test and diagnostic extension (the paper has no counterpart): bound the
+ * grid-barrier waits of later lbm_batch_step calls to poll_limit polls of about
+ * 0.1 us each (0 restores the default, about 3 s), and with skip_arrival != 0 make
+ * block 0 pass the barriers without arriving, so that every other block's wait
+ * runs out.  This exercises the timeout path without any GPU fault: the kernel
+ * stops, lbm_batch_synchronize returns LBM_ERR_TIMEOUT and the batch is poisoned;
+ * the domains' states are then not valid.  LBM_ERR_INVALID_ARG for a NULL batch. */
+lbm_status lbm_batch_set_wait(lbm_batch_handle b, uint32_t poll_limit, int32_t skip_arrival);
+
 /* Chosen tile shape, grid size (blocks) and whether launches go through a CUDA graph. */
 lbm_status lbm_batch_info(lbm_batch_handle b, int32_t* block_x, int32_t* block_y, int32_t* grid_blocks,
                           int32_t* graph_captured);

@@ -227,7 +227,7 @@ lbm_status launch_k(lbm_domain* h, int kind) {
     // pass 1 and the q planes it feeds, timed together
     h->ops->moments_eos(h->dev, h->parity, h->stream);
     h->ops->qflux(h->dev, h->maps, h->stream);
-    h->launches += 2;
+    h->launches += 1;
   } else {
     h->ops->collide_stream(h->dev, h->maps, h->parity, h->stream);
   }

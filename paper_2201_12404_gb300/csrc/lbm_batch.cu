@@ -35,6 +35,8 @@ struct lbm_batch {
   int n_k1 = 0, n_k2 = 0, grid = 0;
   std::map<int64_t, cudaGraphExec_t> graphs;
   bool use_graph = true;
+  unsigned int poll_limit = lbm::kBarrierPollsDefault;
+  int skip_arrival = 0;
   bool poisoned = false;
   int64_t launches = 0;
   std::string err;
@@ -109,6 +111,8 @@ BatchArgs make_args(lbm_batch* b, const DevDomain* jobs, int* parity, int nsteps
   a.barrier = b->d_sync;
   a.error = b->d_sync + 2;
   a.nsteps = nsteps;
+  a.poll_limit = b->poll_limit;
+  a.skip_arrival = b->skip_arrival;
   return a;
 }
 
@@ -246,6 +250,17 @@ lbm_status lbm_batch_synchronize(lbm_batch_handle b) {
     if (st != LBM_OK && worst == LBM_OK) worst = st;
   }
   return worst;
+}
+
+lbm_status lbm_batch_set_wait(lbm_batch_handle b, uint32_t poll_limit, int32_t skip_arrival) {
+  if (!b) return LBM_ERR_INVALID_ARG;
+  if (b->poisoned) return LBM_ERR_STATE;
+  b->poll_limit = poll_limit ? poll_limit : lbm::kBarrierPollsDefault;
+  b->skip_arrival = skip_arrival ? 1 : 0;
+  // the captured graphs hold the previous arguments
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  return LBM_OK;
 }
 
 lbm_status lbm_batch_info(lbm_batch_handle b, int32_t* block_x, int32_t* block_y, int32_t* grid_blocks,

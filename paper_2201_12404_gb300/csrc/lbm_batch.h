@@ -24,7 +24,12 @@ struct BatchArgs {
   unsigned int* barrier;  // [0] arrivals, [1] generation
   unsigned int* error;    // bit 1: a bounded grid-barrier wait gave up
   int nsteps;
+  unsigned int poll_limit;  // polls (each ~0.1 us) before a grid-barrier wait gives up
+  int skip_arrival;         // test switch: block 0 does not arrive at the grid barriers
 };
+
+// Default poll limit of the grid barrier: far above any real wait (~3 s).
+constexpr unsigned int kBarrierPollsDefault = 1u << 25;
 
 // A compiled tile shape of the persistent kernel for one storage precision.
 struct BatchVariant {

@@ -10,31 +10,31 @@
 
 namespace lbm {
 
-// Polls of the grid barrier before the kernel reports a timeout and stops: far
-// above any real wait (each poll sleeps ~0.1 us).
-constexpr unsigned int kBarrierPolls = 1u << 25;
-
 // Bounded grid barrier for a cooperative launch (all blocks co-resident).  The
 // generation is read before arriving; the last block to arrive resets the
-// arrival count and advances the generation.  Returns false when the wait gave
-// up or another block already reported a timeout.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* error) {
+// arrival count and advances the generation.  A wait gives up after `limit`
+// polls (each sleeps ~0.1 us; the default limit is far above any real wait).
+// Returns false when the wait gave up or another block already reported a
+// timeout.  skip (a test switch) makes block 0 pass without arriving or waiting,
+// so that the other blocks' waits run out: the timeout path, with no fault.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* error, unsigned int limit, int skip) {
   __syncthreads();
   __shared__ int ok_s;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     volatile unsigned int* vgen = bar + 1;
     const unsigned int gen = *vgen;
     __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u);
     int ok = 1;
-    if (arrived == gridDim.x - 1) {
+    if (skip && blockIdx.x == 0) {
+      ok = (*(volatile unsigned int*)error & 2u) ? 0 : 1;
+    } else if (atomicAdd(bar, 1u) == gridDim.x - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       unsigned int polls = 0;
       while (*vgen == gen) {
-        if (++polls > kBarrierPolls || (*(volatile unsigned int*)error & 2u)) { ok = 0; break; }
+        if (++polls > limit || (*(volatile unsigned int*)error & 2u)) { ok = 0; break; }
         __nanosleep(100);
       }
     }
@@ -65,19 +65,14 @@ __global__ void __launch_bounds__(BX * BY, sizeof(R) == 4 ? LBM_BATCH_MINBLOCKS_
       if (((a.parity[w.job] + s) & 1) == 0) moments_eos_node<2, 0, S, R, A>(d, xp, yp, 0);
       else moments_eos_node<2, 1, S, R, A>(d, xp, yp, 0);
     }
-    if (!grid_barrier(a.barrier, a.error)) return;
-    // pass 1b: q over the interior tiles, then its ghost layers over the padded tiles
+    if (!grid_barrier(a.barrier, a.error, a.poll_limit, a.skip_arrival)) return;
+    // pass 1b: q over the interior tiles (and the ghosts imaging them)
     for (int it = blockIdx.x; it < a.n_k2; it += gridDim.x) {
       __syncthreads();  // the previous tile's threads are done with s_aux
       const BatchItem w = a.k2[it];
-      qflux_tile<2, BX, BY, 1, R, A, false>(a.jobs[w.job], nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, 0);
+      qflux_tile_staged<2, BX, BY, 1, R, A>(a.jobs[w.job], w.tx * BX, w.ty * BY, 0, s_aux);
     }
-    if (!grid_barrier(a.barrier, a.error)) return;
-    for (int it = blockIdx.x; it < a.n_k1; it += gridDim.x) {
-      const BatchItem w = a.k1[it];
-      qflux_ghost_node<2, A>(a.jobs[w.job], w.tx * BX + threadIdx.x, w.ty * BY + threadIdx.y, 0);
-    }
-    if (!grid_barrier(a.barrier, a.error)) return;
+    if (!grid_barrier(a.barrier, a.error, a.poll_limit, a.skip_arrival)) return;
     for (int it = blockIdx.x; it < a.n_k2; it += gridDim.x) {
       __syncthreads();  // the previous tile's threads are done with s_aux and s_h
       const BatchItem w = a.k2[it];
@@ -87,7 +82,7 @@ __global__ void __launch_bounds__(BX * BY, sizeof(R) == 4 ? LBM_BATCH_MINBLOCKS_
       else
         collide_tile<2, BX, BY, 1, 1, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, s_h, nullptr, 0);
     }
-    if (!grid_barrier(a.barrier, a.error)) return;
+    if (!grid_barrier(a.barrier, a.error, a.poll_limit, a.skip_arrival)) return;
   }
   // every block is past the last barrier: block 0 records the jobs' new parities
   if (blockIdx.x == 0 && (a.nsteps & 1)) {

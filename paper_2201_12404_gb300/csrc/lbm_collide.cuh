@@ -638,75 +638,155 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   return true;
 }
 
-// Pass 1b on one tile of interior nodes whose origin is (x0, y0, z0): q_a = rho v_a^3
-// (Eq. (correction) with P0/rho = cs^2) at every node of the tile, with v = (j +
-// F/2)/rho the fluid velocity of the exact-difference forcing and F the force of
-// Eq. (Kforce_final) from the staged (rho, psi) halo tile (the stencil of pass 2),
-// j and rho those pass 1 wrote for the node.  kTma: the halo tile comes from one
-// TMA copy on `bar` (phase `phase`); otherwise each warp loads halo rows.  The
-// ghost layers of q are filled afterwards from their images.  Returns false when
-// the halo copy did not arrive within the poll limit.
-template <int D, int BX, int BY, int BZ, typename R, typename A, bool kTma>
-__device__ __forceinline__ bool qflux_tile(const DevDomain& d, const TileMaps* maps, int x0, int y0, int z0,
-                                           Two<A>* s_aux, unsigned long long* bar, uint32_t phase) {
-  constexpr int NT = BX * BY * BZ;
-  using H = Halo<D, BX, BY, BZ>;
-  const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
-  if (kTma) {
-    if (tid == 0) {
-      mbar_arrive_expect_tx(bar, (uint32_t)(H::HN * sizeof(Two<A>)));
-      tma_load_tile<D, A>(s_aux, &maps->aux, bar, x0, y0, z0);
-    }
-  } else {
-    const Two<A>* a2 = (const Two<A>*)d.aux;
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int r = warp; r < H::HY * H::HZ; r += NT / 32) {
-      const int yp = y0 + r % H::HY, zp = z0 + r / H::HY;
-      const bool row_ok = yp < d.py && zp < d.pz;
-      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
-      for (int hx = lane; hx < H::HX; hx += 32) {
-        const bool ok = row_ok && x0 + hx < d.px;
-        s_aux[r * H::HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
-      }
-    }
-    __syncthreads();
+// Padded coordinate of the ghost node that images interior coordinate x along an
+// axis of n >= 5 nodes, or -1 when no ghost does (x more than 1 node from both
+// faces); *wall is set when that ghost mirrors x across a bounce-back wall.  The
+// ghost layers are 2 nodes wide: a periodic ghost sits n nodes away, a wall ghost
+// is the mirror image across the half-way wall (the inverse of ghost_image).
+__device__ __forceinline__ int ghost_of(int x, int n, int wlo, int whi, bool* wall) {
+  if (x <= 1) {
+    if (wlo) { *wall = true; return 1 - x; }
+    return x + n + 2;
   }
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
-  const bool active = x < d.nx && y < d.ny && z < d.nz;
-  if (kTma && !mbar_wait_bounded(bar, phase, kTileWaitPolls)) {
-    // every thread waits, so that the block cannot retire while the copy is in flight
-    if (tid == 0) atomicOr(d.flags, 2u);
-    mbar_wait_bounded(bar, phase, kTileWaitPolls);
-    return false;
+  if (x >= n - 2) {
+    if (whi) { *wall = true; return 2 * n + 1 - x; }
+    return x - n + 2;
   }
-  if (!active) return true;
-  const int sc = (threadIdx.x + 2) + H::HX * ((threadIdx.y + 2) + H::HY * (D == 3 ? threadIdx.z + 2 : 0));
-  const R rho = (R)s_aux[sc].x;
-  R F[3];
-  stencil_force<D, R, A>(phys<R>(d), rho, [&](int dx, int dy, int dz) { return s_aux[sc + dx + H::HX * (dy + H::HY * dz)]; },
-                         F);
-  A* aux = (A*)d.aux;
-  const long long pn = pnode_of<D>(d, x, y, z);
-  const R inv = (R)1 / rho;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const R v = ((R)aux[(2 + D + a) * d.PN + pn] + (R)0.5 * F[a]) * inv;
-    aux[(2 + a) * d.PN + pn] = (A)(rho * v * v * v);
-  }
-  return true;
+  return -1;
 }
 
-template <int D, typename R, typename A>
-__global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz)
-qflux_tile_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
-  constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
-  using H = Halo<D, BX, BY, BZ>;
-  __shared__ __align__(128) Two<A> s_aux[H::HN];
-  __shared__ __align__(8) unsigned long long tile_bar;
-  if (threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z) == 0) mbar_init(&tile_bar, 1);
+// Pass 1b on one tile of interior nodes of extents EX x EY x EZ whose origin is
+// (x0, y0, z0), run by TX x TY threads, each walking TK nodes (along z in 3-D,
+// along y in 2-D): q_a = rho v_a^3 (Eq. (correction) with P0/rho = cs^2) with v =
+// (j + F/2)/rho the fluid velocity of the exact-difference forcing, F the force of
+// Eq. (Kforce_final) from the staged (rho, psi) halo tile s_aux (pass 2's stencil),
+// j (loaded by qflux_load_j) and rho those pass 1 wrote for the node.  The node's q
+// also goes to the ghost nodes that image it (negated across a wall: the no-slip
+// image of pass 1's fields).
+template <int D, int TX, int TY, int TK> struct QTileShape {
+  static constexpr int EY = D == 3 ? TY : TY * TK, EZ = D == 3 ? TK : 1;
+  static constexpr int HX = TX + 4, HY = EY + 4, HZ = D == 3 ? EZ + 4 : 1;
+};
+
+// The momenta j of this thread's TK nodes of the tile at (x0, y0, z0) (0 outside).
+template <int D, int TX, int TY, int TK, typename A>
+__device__ __forceinline__ void qflux_load_j(const DevDomain& d, int x0, int y0, int z0, A (&jn)[TK][D]) {
+  const A* aux = (const A*)d.aux;
+  const int x = x0 + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < TK; ++k) {
+    const int y = y0 + (D == 3 ? (int)threadIdx.y : (int)threadIdx.y + TY * k), z = z0 + (D == 3 ? k : 0);
+    const bool in = x < d.nx && y < d.ny && z < d.nz;
+    const long long pn = in ? pnode_of<D>(d, x, y, z) : 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) jn[k][a] = in ? aux[(2 + D + a) * d.PN + pn] : (A)0;
+  }
+}
+
+template <int D, int TX, int TY, int TK, typename R, typename A>
+__device__ __forceinline__ void qflux_nodes(const DevDomain& d, int x0, int y0, int z0, const Two<A>* s_aux,
+                                            const A (&jn)[TK][D]) {
+  using SH = QTileShape<D, TX, TY, TK>;
+  A* aux = (A*)d.aux;
+  const int x = x0 + threadIdx.x;
+  bool gw_x = false;
+  const int gx = ghost_of(x, d.nx, d.wall_lo[0], d.wall_hi[0], &gw_x);
+#pragma unroll
+  for (int k = 0; k < TK; ++k) {
+    const int ly = D == 3 ? threadIdx.y : threadIdx.y + TY * k, lz = D == 3 ? k : 0;
+    const int y = y0 + ly, z = z0 + lz;
+    if (!(x < d.nx && y < d.ny && z < d.nz)) continue;
+    const int sc = (threadIdx.x + 2) + SH::HX * ((ly + 2) + SH::HY * (D == 3 ? lz + 2 : 0));
+    const R rho = (R)s_aux[sc].x;
+    R F[3];
+    stencil_force<D, R, A>(phys<R>(d), rho,
+                           [&](int dx, int dy, int dz) { return s_aux[sc + dx + SH::HX * (dy + SH::HY * dz)]; }, F);
+    const long long pn = pnode_of<D>(d, x, y, z);
+    const R inv = (R)1 / rho;
+    A q[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const R v = ((R)jn[k][a] + (R)0.5 * F[a]) * inv;
+      q[a] = (A)(rho * v * v * v);
+      aux[(2 + a) * d.PN + pn] = q[a];
+    }
+    // the ghost nodes imaging this node: every combination of its own or its ghost
+    // coordinate on each axis that has a ghost, other than its own on all of them
+    bool gw_y = false, gw_z = false;
+    const int gy = ghost_of(y, d.ny, d.wall_lo[1], d.wall_hi[1], &gw_y);
+    const int gz = D == 3 ? ghost_of(z, d.nz, d.wall_lo[2], d.wall_hi[2], &gw_z) : -1;
+    if (gx < 0 && gy < 0 && gz < 0) continue;
+#pragma unroll 1
+    for (int m = 1; m < (1 << D); ++m) {
+      if (((m & 1) && gx < 0) || ((m & 2) && gy < 0) || ((m & 4) && gz < 0)) continue;
+      const int cx = (m & 1) ? gx : x + 2, cy = (m & 2) ? gy : y + 2, cz = D == 3 ? ((m & 4) ? gz : z + 2) : 0;
+      const bool flip = ((m & 1) && gw_x) || ((m & 2) && gw_y) || ((m & 4) && gw_z);
+      const long long g = (long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz);
+#pragma unroll
+      for (int a = 0; a < D; ++a) aux[(2 + a) * d.PN + g] = flip ? -q[a] : q[a];
+    }
+  }
+}
+
+// Pass 1b on one tile with warp-staged halo rows (the batched kernel's form).
+template <int D, int TX, int TY, int TK, typename R, typename A>
+__device__ __forceinline__ void qflux_tile_staged(const DevDomain& d, int x0, int y0, int z0, Two<A>* s_aux) {
+  using SH = QTileShape<D, TX, TY, TK>;
+  constexpr int NT = TX * TY;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const Two<A>* a2 = (const Two<A>*)d.aux;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int r = warp; r < SH::HY * SH::HZ; r += NT / 32) {
+    const int yp = y0 + r % SH::HY, zp = z0 + r / SH::HY;
+    const bool row_ok = yp < d.py && zp < d.pz;
+    const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
+    for (int hx = lane; hx < SH::HX; hx += 32) {
+      const bool ok = row_ok && x0 + hx < d.px;
+      s_aux[r * SH::HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
+    }
+  }
   __syncthreads();
-  qflux_tile<D, BX, BY, BZ, R, A, true>(d, &maps, blockIdx.x * BX, blockIdx.y * BY, D == 3 ? blockIdx.z * BZ : 0,
-                                         s_aux, &tile_bar, 0);
+  A jn[TK][D];
+  qflux_load_j<D, TX, TY, TK, A>(d, x0, y0, z0, jn);
+  qflux_nodes<D, TX, TY, TK, R, A>(d, x0, y0, z0, s_aux, jn);
+}
+
+// Pass 1b, one QTile tile per block: the halo tile comes from one TMA copy while
+// the threads load their nodes' momenta.  (A persistent form with two halo buffers,
+// the next tile's copy in flight during the current one, was slower: its two
+// 41 KB buffers leave two blocks per SM, and the stencil's shared-memory reads,
+// not the copy latency, set the pace.)  A wait that gives up sets bit 1 of the
+// error word; the block then waits (bounded) for the copy and stops.
+template <int D, typename R, typename A>
+__global__ void __launch_bounds__(QTile<D, 2 * sizeof(A)>::TX * QTile<D, 2 * sizeof(A)>::TY)
+qflux_tile_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
+  using T = QTile<D, 2 * sizeof(A)>;
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  Two<A>* s_aux = (Two<A>*)smem_dyn;  // [z][y][x] (rho, psi)
+  unsigned long long* bar = (unsigned long long*)(smem_dyn + ((T::HN * sizeof(Two<A>) + 15) / 16) * 16);
+  const int tid = threadIdx.x + T::TX * threadIdx.y;
+  const int x0 = blockIdx.x * T::EX, y0 = blockIdx.y * T::EY, z0 = D == 3 ? blockIdx.z * T::EZ : 0;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_arrive_expect_tx(bar, (uint32_t)(T::HN * sizeof(Two<A>)));
+    tma_load_tile<D, A>(s_aux, &maps.aux_q, bar, x0, y0, z0);
+  }
+  __syncthreads();
+  A jn[T::TK][D];
+  qflux_load_j<D, T::TX, T::TY, T::TK, A>(d, x0, y0, z0, jn);
+  if (!mbar_wait_bounded(bar, 0, kTileWaitPolls)) {
+    // every thread waits, so that the block cannot retire while the copy is in flight
+    if (tid == 0) atomicOr(d.flags, 2u);
+    mbar_wait_bounded(bar, 0, kTileWaitPolls);
+    return;
+  }
+  qflux_nodes<D, T::TX, T::TY, T::TK, R, A>(d, x0, y0, z0, s_aux, jn);
+}
+
+// Dynamic shared memory of the pass-1b kernel: the halo tile and its mbarrier.
+template <int D, typename A>
+constexpr size_t qflux_dyn_smem() {
+  return ((QTile<D, 2 * sizeof(A)>::HN * sizeof(Two<A>) + 15) / 16) * 16 + 16;
 }
 
 template <int D, int P, typename S, typename R, typename A>

@@ -4,8 +4,10 @@
 // Data layout in HBM (one domain):
 //   populations  f[i * N + node]          SoA, node = x + nx*(y + ny*z), one A-A buffer
 //   auxiliary    aux2[pnode] = (rho, psi) interleaved pairs, then q_a[pnode] planes
-//                                         (element offset (2 + a) * PN); padded by a 2-node
-//                                         ghost layer on every axis (2-D: z not padded)
+//                                         (element offset (2 + a) * PN), then the bare
+//                                         momentum j_a[pnode] (offset (2 + D + a) * PN);
+//                                         padded by a 2-node ghost layer on every axis
+//                                         (2-D: z not padded)
 // The A-A pattern keeps one population buffer: an even step (parity 0) reads and
 // writes the node's own slots (writing direction i into slot Q-1-i), an odd step
 // (parity 1) reads the neighbours' slots and writes back into them, so that after
@@ -110,8 +112,22 @@ struct DevDomain {
 
 // The tensor maps of the collide kernel's TMA loads (passed as a kernel parameter).
 struct TileMaps {
-  CUtensorMap aux;  // (rho, psi) halo tile
-  CUtensorMap q;    // q_a boxes
+  CUtensorMap aux;    // (rho, psi) halo tile of pass 2
+  CUtensorMap q;      // q_a boxes of pass 2
+  CUtensorMap aux_q;  // (rho, psi) halo tile of pass 1b (QTile)
+};
+
+// Tile of pass 1b (the q kernel): TX x TY threads; in 3-D each thread walks TK
+// nodes along z (tile TX x TY x TK), in 2-D along y (tile TX x TY*TK).  Taller
+// tiles than pass 2's keep the staged halo small against the tile: pass 1b does
+// little arithmetic per node, so the halo traffic would dominate.  kPairBytes is
+// the size of one staged (rho, psi) pair.
+template <int D, int kPairBytes> struct QTile {
+  static constexpr int TX = D == 3 ? 32 : 64, TY = D == 3 ? 8 : 4;
+  static constexpr int TK = D == 3 ? (kPairBytes == 8 ? 8 : 4) : 4;
+  static constexpr int EX = TX, EY = D == 3 ? TY : TY * TK, EZ = D == 3 ? TK : 1;  // tile extents
+  static constexpr int HX = EX + 4, HY = EY + 4, HZ = D == 3 ? EZ + 4 : 1;         // with the halo
+  static constexpr int HN = HX * HY * HZ;
 };
 
 // float16-deviation storage: a slot holds delta = f/(w_i rho_w) - 1 in half

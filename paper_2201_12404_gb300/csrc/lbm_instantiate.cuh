@@ -20,10 +20,19 @@ struct Launch {
     else moments_eos_kernel<D, 1, S, R, A><<<grd, blk, 0, s>>>(d);
   }
   static void qflux(const DevDomain& d, const TileMaps& maps, cudaStream_t s) {
-    dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
-    qflux_tile_kernel<D, R, A><<<node_grid(d), blk, 0, s>>>(d, maps);
-    dim3 grd((d.px + blk.x - 1) / blk.x, (d.py + blk.y - 1) / blk.y, (d.pz + blk.z - 1) / blk.z);
-    qflux_ghost_kernel<D, A><<<grd, blk, 0, s>>>(d);
+    using T = QTile<D, 2 * sizeof(A)>;
+    constexpr size_t smem = qflux_dyn_smem<D, A>();
+    auto k = qflux_tile_kernel<D, R, A>;
+    constexpr int kMaxDev = 64;
+    static bool opted_in[kMaxDev] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem > 48 * 1024 && (dev < 0 || dev >= kMaxDev || !opted_in[dev])) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (dev >= 0 && dev < kMaxDev) opted_in[dev] = true;
+    }
+    const dim3 grd((d.nx + T::EX - 1) / T::EX, (d.ny + T::EY - 1) / T::EY, (d.nz + T::EZ - 1) / T::EZ);
+    k<<<grd, dim3(T::TX, T::TY), smem, s>>>(d, maps);
   }
   static void collide_stream(const DevDomain& d, const TileMaps& maps, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);

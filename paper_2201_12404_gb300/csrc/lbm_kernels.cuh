@@ -5,8 +5,8 @@
 //                                  Peng-Robinson pseudo-potential; writes (rho, psi) and
 //                                  j to the padded auxiliary fields, ghosts included.
 //  qflux_tile_kernel     (pass 1b) q = rho v^3, v = (j + F/2)/rho the fluid velocity,
-//                                  F from the (rho, psi) halo tile (Eq. Kforce_final);
-//                                  qflux_ghost_kernel fills the ghost layers of q.
+//                                  F from the (rho, psi) halo tile (Eq. Kforce_final),
+//                                  written to the node and the ghosts imaging it.
 //  collide_stream_kernel (pass 2)  gather f, force from the auxiliary halo
 //                                  (Eq. Kforce_final), Phi (Eq. correction), f^eq and
 //                                  f* (Eqs. LBMeq, LBMstar), k/s/h split (Appendix A),
@@ -217,36 +217,6 @@ __device__ __forceinline__ void aux_force(const DevDomain& d, int x, int y, int 
   const R spsi_c = psi_sign<R>(phys<R>(d), (R)a2[pc].x) * (R)a2[pc].y;
   for (int a = 0; a < 3; ++a)
     F[a] = a < D ? -((R)2 * spsi_c * g4[a] + phys<R>(d).kappa * rho * g3[a]) + rho * phys<R>(d).g[a] : (R)0;
-}
-
-// ---------------------------------------------------------------------------
-// Ghost layers of the q planes after pass 1b (qflux_tile): a ghost node takes the q
-// of the interior node it images, negated across a wall (no-slip image), as pass 1
-// does for its fields.
-// ---------------------------------------------------------------------------
-template <int D, typename A>
-__device__ __forceinline__ void qflux_ghost_node(const DevDomain& d, int xp, int yp, int zp) {
-  if (xp >= d.nx + 4 || yp >= d.py || zp >= d.pz) return;
-  const bool inside = xp >= 2 && xp < d.nx + 2 && yp >= 2 && yp < d.ny + 2 && (D == 2 || (zp >= 2 && zp < d.nz + 2));
-  if (inside) return;
-  bool flip = false;
-  const int x = ghost_image(xp, d.nx, d.wall_lo[0], d.wall_hi[0], &flip);
-  const int y = ghost_image(yp, d.ny, d.wall_lo[1], d.wall_hi[1], &flip);
-  const int z = D == 3 ? ghost_image(zp, d.nz, d.wall_lo[2], d.wall_hi[2], &flip) : 0;
-  A* aux = (A*)d.aux;
-  const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * (long long)zp);
-  const long long pi = pnode_of<D>(d, x, y, z);
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const A q = aux[(2 + a) * d.PN + pi];
-    aux[(2 + a) * d.PN + pn] = flip ? -q : q;
-  }
-}
-
-template <int D, typename A>
-__global__ void __launch_bounds__(256) qflux_ghost_kernel(DevDomain d) {
-  qflux_ghost_node<D, A>(d, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
-                         blockIdx.z * blockDim.z + threadIdx.z);
 }
 
 // ---------------------------------------------------------------------------

@@ -88,19 +88,17 @@ inline tensor_map_encode_fn tensor_map_encoder(const char** why) {
 }
 
 // Tensor map over the interleaved (rho, psi) pairs at the start of d.aux, with a
-// box of one halo tile (Blocks::bx + 4, Blocks::by + 4[, Blocks::bz + 4]) of pairs.
+// box of one halo tile of `tile` pairs per axis.
 // float32 pairs are single 8-byte elements of a (px, py[, pz]) tensor; float64
 // pairs are the 16-byte innermost dimension of a (2, px, py[, pz]) tensor (a box's
 // innermost extent must be a multiple of 16 bytes).  Returns false with a message
 // when the driver refuses it.
-inline bool make_aux_map(CUtensorMap* map, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
+inline bool make_aux_map(CUtensorMap* map, const DevDomain& d, int D, size_t elem_bytes, const cuuint32_t tile[3],
+                         const char** why) {
   const tensor_map_encode_fn encode = tensor_map_encoder(why);
   if (!encode) return false;
   const size_t pair_bytes = 2 * elem_bytes;
   const cuuint64_t ext[3] = {(cuuint64_t)d.px, (cuuint64_t)d.py, (cuuint64_t)d.pz};
-  const cuuint32_t tile[3] = {D == 3 ? (cuuint32_t)Blocks<3>::bx + 4 : (cuuint32_t)Blocks<2>::bx + 4,
-                              D == 3 ? (cuuint32_t)Blocks<3>::by + 4 : (cuuint32_t)Blocks<2>::by + 4,
-                              (cuuint32_t)Blocks<3>::bz + 4};
   cuuint64_t dims[4], strides[3];
   cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
   cuuint32_t rank = 0;
@@ -185,8 +183,26 @@ inline void fill_geometry(DevDomain& d, const lbm_params& p, int D, size_t pop_b
   fill_slot_offsets(d, D, pop_bytes);
 }
 
+// The halo box of QTile<D, pair bytes> for pass 1b.
+template <int D, int kPairBytes>
+inline void qtile_box(cuuint32_t box[3]) {
+  using T = QTile<D, kPairBytes>;
+  box[0] = T::HX; box[1] = T::HY; box[2] = T::HZ;
+}
+
 inline bool make_tile_maps(TileMaps* m, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
-  return make_aux_map(&m->aux, d, D, elem_bytes, why) && make_q_map(&m->q, d, D, elem_bytes, why);
+  // pass 2: a tile of Blocks<D> nodes with a 2-node halo
+  const cuuint32_t tile[3] = {D == 3 ? (cuuint32_t)Blocks<3>::bx + 4 : (cuuint32_t)Blocks<2>::bx + 4,
+                              D == 3 ? (cuuint32_t)Blocks<3>::by + 4 : (cuuint32_t)Blocks<2>::by + 4,
+                              (cuuint32_t)Blocks<3>::bz + 4};
+  cuuint32_t qbox[3];
+  if (D == 3) {
+    if (elem_bytes == 4) qtile_box<3, 8>(qbox); else qtile_box<3, 16>(qbox);
+  } else {
+    if (elem_bytes == 4) qtile_box<2, 8>(qbox); else qtile_box<2, 16>(qbox);
+  }
+  return make_aux_map(&m->aux, d, D, elem_bytes, tile, why) && make_aux_map(&m->aux_q, d, D, elem_bytes, qbox, why) &&
+         make_q_map(&m->q, d, D, elem_bytes, why);
 }
 
 // Final fixed-order reduction of the diagnostic partial sums (lbm_d2q9.cu).

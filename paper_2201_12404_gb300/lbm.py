@@ -112,6 +112,7 @@ def load():
                 "lbm_batch_synchronize": (st, [H]),
                 "lbm_batch_tune": (st, [H, ctypes.c_int32, ctypes.c_char_p]),
                 "lbm_batch_info": (st, [H] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+                "lbm_batch_set_wait": (st, [H, ctypes.c_uint32, ctypes.c_int32]),
                 "lbm_batch_destroy": (st, [H]),
                 "lbm_batch_last_error": (ctypes.c_char_p, [H]),
             }
@@ -386,6 +387,9 @@ class Batch:
 
     def lbm_batch_tune(self, trial_steps: int, cache_path=None):
         self._c(load().lbm_batch_tune(self.handle, int(trial_steps), cache_path.encode() if cache_path else None))
+
+    def lbm_batch_set_wait(self, poll_limit: int, skip_arrival: bool = False):
+        self._c(load().lbm_batch_set_wait(self.handle, int(poll_limit), 1 if skip_arrival else 0))
 
     def lbm_batch_info(self):
         v = [ctypes.c_int32() for _ in range(4)]

@@ -388,8 +388,8 @@ def crown_study(quick=False, wl=None, t_end_tau=2.0, samples=100, precision=lbm.
 # Re = 2 U0 R0 / nu_l, in a 24 R0 x 12 R0 box with a film h = R0, T/Tc = 0.59, nu_v = 15 nu_l.
 PAPER_2D_CASES = ((57, 4000), (93, 4000), (238, 4000), (93, 100))
 # sigma at T/Tc = 0.59 with a = 0.003 and kappa = 0.01: the Laplace-law sweep of
-# surface_tension_study gives 0.202 at 0.55 and 0.168 at 0.6; linear in between.
-SIGMA_T059 = 0.175
+# surface_tension_study gives 0.203 at 0.55 and 0.169 at 0.6; linear in between.
+SIGMA_T059 = WL.SIGMA_T059
 
 
 def paper_2d_impacts(R0=100.0, sigma=SIGMA_T059, cases=PAPER_2D_CASES):

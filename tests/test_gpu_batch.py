@@ -108,3 +108,43 @@ def test_batch_rejects_mixed_precision_and_3d():
         lbm.Batch([a, a])
     for d in (a, b, c):
         d.close()
+
+
+def test_a_grid_barrier_wait_that_runs_out_reports_timeout_and_the_device_stays_usable():
+    """The bounded device-side waits of the batched kernel, made to run out without
+    any fault: block 0 skips its arrival at the grid barriers (a test switch), the
+    other blocks' waits give up after a short poll limit (~2 ms), the kernel stops
+    and lbm_batch_synchronize reports LBM_ERR_TIMEOUT.  A fresh batch on the same
+    device then steps exactly as single domains do."""
+    c = case(2, 16, 16, precision=lbm.LBM_FP32)
+    f0 = drop_state(c).astype(np.float32).astype(np.float64)
+    doms = []
+    for _ in range(2):
+        d = lbm.Domain(lbm_params(c))
+        d.lbm_write_populations(f0)
+        doms.append(d)
+    b = lbm.Batch(doms)
+    assert b.lbm_batch_info()["grid"] >= 2
+    b.lbm_batch_set_wait(20000, skip_arrival=True)
+    b.lbm_batch_step(2)
+    with pytest.raises(lbm.LBMError) as e:
+        b.lbm_batch_synchronize()
+    assert e.value.status == lbm.LBM_ERR_TIMEOUT
+    b.close()
+    for d in doms:
+        d.close()
+    # the context is intact: a fresh batch gives the single-domain result
+    alone = lbm.Domain(lbm_params(c))
+    alone.lbm_write_populations(f0)
+    fresh = [lbm.Domain(lbm_params(c)) for _ in range(2)]
+    for d in fresh:
+        d.lbm_write_populations(f0)
+    with lbm.Batch(fresh) as b2:
+        b2.lbm_batch_step(2)
+        b2.lbm_batch_synchronize()
+    alone.lbm_step(2)
+    ref = alone.lbm_read_populations()
+    for d in fresh:
+        assert np.array_equal(d.lbm_read_populations(), ref)
+    for d in fresh + [alone]:
+        d.close()
