@@ -266,25 +266,25 @@ def algorithmic_bytes_k2(wl, pop_bytes, aux_bytes):
     return wl.N * (2 * Q * pop_bytes + (2 + wl.D) * aux_bytes)
 
 
-def serving_sample(n_jobs, scale=0.05, seed=None):
-    """The served-job part of the metric: a short run of the continuous-batching
-    server (seeded Poisson arrivals at ~80% load of mixed D2Q9/D3Q27 jobs, FP32,
-    1,000-10,000 steps per job scaled by `scale`, admission by footprint against
-    half of the free HBM)."""
+def serving_sample(n_jobs, scale=0.25, seed=None):
+    """The served-job part of the metric: a run of the continuous-batching server
+    (seeded Poisson arrivals offering 80% of 12 GLUPS of mixed D2Q9/D3Q27 jobs, FP32,
+    1,000-10,000 steps per job scaled by `scale`, admission by footprint against half
+    of the free HBM)."""
     import torch
     from paper_2201_12404_gb300 import inputs as I
     from paper_2201_12404_gb300 import serve as SV
     seed = I.SEED_BASE if seed is None else seed
     jobs = SV.random_jobs(n_jobs, seed, scale)
-    total_lups = sum(j.N * j.steps for j in jobs)
-    rate = 0.8 * len(jobs) / (total_lups / 9e9)
+    rate = SV.rate_for_load(jobs)
     free, _ = torch.cuda.mem_get_info()
     rep = SV.serve(jobs, SV.poisson_arrivals(len(jobs), rate, seed), int(0.5 * free))
     return {"p50_latency_s": rep["p50_latency_s"], "p99_latency_s": rep["p99_latency_s"],
             "aggregate_mlups": rep["aggregate_mlups"], "jobs": rep["jobs"], "completed": rep["completed"],
             "failed": rep["failed"], "admitted_while_busy": rep["admissions_while_busy"], "wall_s": rep["wall_s"],
+            "batch_builds": rep.get("batch_builds"),
             "what": f"{n_jobs} seeded Poisson arrivals (rate {rate:.2f}/s), half D2Q9 64^2-1024^2, half D3Q27 "
-                    f"64^3-256^3, steps 1,000-10,000 x {scale}, FP32"}
+                    f"64^3-256^3, steps 1,000-10,000 x {scale} (that fraction of each job's steps), FP32"}
 
 
 def algorithmic_bytes_k1(wl, pop_bytes, aux_bytes):
@@ -418,7 +418,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if world == 1 and args.serve_jobs > 0:
-        line["serving"] = serving_sample(args.serve_jobs)
+        line["serving"] = serving_sample(args.serve_jobs, args.serve_scale)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(wl)
     print(json.dumps(line), flush=True)
@@ -432,8 +432,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=40,
+    ap.add_argument("--serve-jobs", type=int, default=200,
                     help="jobs of the served-latency sample added to the line at N = 1 (0: none)")
+    ap.add_argument("--serve-scale", type=float, default=0.25,
+                    help="fraction of each served job's 1,000-10,000 steps")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16dev"], default="fp32",
                     help="population storage/arithmetic of the timed path (fp32 is the headline)")
     ap.add_argument("--workload", default="drop3d", choices=["drop3d", "drop3d-small", "drop2d"],

@@ -4,9 +4,10 @@ A request is a simulation job (lattice, size, temperature, viscosity, drop/film
 geometry, step count).  The server keeps every admitted job's populations
 resident on the GPU, admits waiting jobs whenever slots and HBM free up
 (admission by lbm_footprint_bytes against a byte budget), and advances the
-resident set in time slices: all resident D2Q9 jobs of one precision through one
-persistent batched launch (lbm_batch_step), every D3Q27 job on its own CUDA
-stream, so that their work overlaps on the device.  A job whose density turns
+resident set in time slices: the resident D2Q9 jobs through one persistent
+batched launch (lbm_batch_step) kept across slices, every D3Q27 job on its own
+CUDA stream, so that their work overlaps on the device; the host runs a slice
+ahead of the device and polls completions with events.  A job whose density turns
 non-finite or non-positive ends as failed (expected at the lowest viscosities)
 and frees its slot.  Reported: p50/p99 latency (arrival to result), aggregate
 MLUPS, failures.
@@ -82,6 +83,16 @@ def random_jobs(n_jobs, seed=I.SEED_BASE, scale=1.0):
     return jobs
 
 
+# Device throughput the arrival rate is sized against (lattice updates per second):
+# about that of the step on a large D3Q27 domain, which dominates the mix's work.
+CAPACITY_LUPS = 12e9
+
+
+def rate_for_load(jobs, load=0.8, capacity=CAPACITY_LUPS):
+    """Arrival rate (jobs per second) that offers `load` times the capacity."""
+    return load * len(jobs) / (sum(j.N * j.steps for j in jobs) / capacity)
+
+
 def poisson_arrivals(n_jobs, rate_per_s, seed):
     """Arrival times (seconds from the start) of a seeded Poisson process."""
     gaps = I.rng(seed + 1).exponential(1.0 / rate_per_s, size=n_jobs)
@@ -131,12 +142,28 @@ class Scheduler:
 # ---------------------------------------------------------------------------
 
 class GpuExecutor:
-    """Resident domains, one batch for the D2Q9 jobs of a slice, streams for D3Q27."""
+    """Resident domains and their slices of steps.
 
-    def __init__(self):
+    Every D2Q9 job runs on one shared stream, the resident D2Q9 jobs with at least a
+    slice of steps left as one persistent batch (lbm_batch_step), rebuilt only when
+    that set changes; a D2Q9 job with fewer steps left finishes them with its own
+    lbm_step on the same stream.  Every D3Q27 job has a stream of its own.  The host
+    enqueues slice after slice and stays at most `in_flight` slices ahead of the
+    device (it waits on the events of older slices); a job's completion is an event
+    recorded after its last step, polled without blocking, and an instability
+    surfaces through the library's non-blocking flag poll (lbm_step(0))."""
+
+    def __init__(self, in_flight=2):
+        import torch
+        self.torch = torch
         lbm.load()
-        self.doms = {}        # job_id -> (spec, Domain, remaining steps)
+        self.in_flight = in_flight
+        self.s2 = torch.cuda.Stream()     # all D2Q9 jobs
+        self.doms = {}                   # job_id -> [spec, Domain, remaining steps, stream, done event]
         self.coex = {}
+        self.batch, self.batch_ids = None, ()
+        self.slices = []                 # events of the slices in flight
+        self.batch_builds = 0
 
     def _coexistence(self, T):
         if T not in self.coex:
@@ -146,55 +173,83 @@ class GpuExecutor:
     def start(self, spec: JobSpec):
         rv, rl, _ = self._coexistence(spec.T_over_Tc)
         wl = spec.workload()
-        dom = lbm.Domain(spec.params(rv=rv, rl=rl))
+        stream = self.s2 if spec.D == 2 else self.torch.cuda.Stream()
+        p = spec.params(rv=rv, rl=rl)
+        p.stream = stream.cuda_stream
+        dom = lbm.Domain(p)
         rho, u = WL.initial_fields(wl, rv, rl)
         dom.lbm_init_fields(rho, u)
-        self.doms[spec.job_id] = [spec, dom, spec.steps]
+        self.doms[spec.job_id] = [spec, dom, spec.steps, stream, None]
+
+    def _drop_batch(self):
+        if self.batch is not None:
+            self.batch.close()
+        self.batch, self.batch_ids = None, ()
 
     def slice(self, slice_steps):
-        """Advance every resident job by up to slice_steps; returns the finished and failed
-        job ids as (finished: {id: (rho, u)}, failed: {id: message})."""
-        two = [v for v in self.doms.values() if v[0].D == 2]
-        three = [v for v in self.doms.values() if v[0].D == 3]
-        failed = {}
+        """Enqueue up to slice_steps steps of every resident job that has steps left."""
+        while len(self.slices) >= self.in_flight:
+            for ev in self.slices.pop(0):
+                ev.synchronize()
+        evs = []
+        two = [v for v in self.doms.values() if v[0].D == 2 and v[2] > 0]
+        full = tuple(sorted(v[0].job_id for v in two if v[2] >= slice_steps))
+        if full:
+            if full != self.batch_ids:
+                self._drop_batch()
+                self.batch = lbm.Batch([self.doms[j][1] for j in full])
+                self.batch_ids = full
+                self.batch_builds += 1
+            self.batch.lbm_batch_step(slice_steps)
+            for j in full:
+                self.doms[j][2] -= slice_steps
+        for v in two:
+            if 0 < v[2] < slice_steps:
+                v[1].lbm_step(v[2])
+                v[2] = 0
         if two:
-            k = min(slice_steps, min(v[2] for v in two))
-            by_prec = {}
+            ev = self.torch.cuda.Event()
+            ev.record(self.s2)
+            evs.append(ev)
             for v in two:
-                by_prec.setdefault(v[0].precision, []).append(v)
-            batches = []
-            for group in by_prec.values():
-                b = lbm.Batch([v[1] for v in group])
-                b.lbm_batch_step(k)
-                batches.append((b, group))
-            for v in two:
+                if v[2] == 0 and v[4] is None:
+                    v[4] = ev
+        for v in self.doms.values():
+            if v[0].D == 3 and v[2] > 0:
+                k = min(slice_steps, v[2])
+                v[1].lbm_step(k)
                 v[2] -= k
-        for v in three:
-            k3 = min(slice_steps, v[2])
+                ev = self.torch.cuda.Event()
+                ev.record(v[3])
+                evs.append(ev)
+                if v[2] == 0:
+                    v[4] = ev
+        self.slices.append(evs)
+
+    def idle(self):
+        """Whether no resident job has steps left to enqueue."""
+        return all(v[2] == 0 for v in self.doms.values())
+
+    def poll(self):
+        """Jobs that have finished or failed, without waiting for running work:
+        (finished: {id: (rho, u)}, failed: {id: message})."""
+        finished, failed = {}, {}
+        for jid, (spec, dom, rem, stream, done) in list(self.doms.items()):
             try:
-                v[1].lbm_step(k3)
-            except lbm.LBMError as e:
-                failed[v[0].job_id] = str(e)
-            v[2] -= k3
-        if two:
-            for b, group in batches:
-                try:
-                    b.lbm_batch_synchronize()
-                except lbm.LBMError:
-                    pass  # the failing domains are found below
-                b.close()
-        finished = {}
-        for jid, (spec, dom, rem) in list(self.doms.items()):
-            if jid in failed:
-                continue
-            try:
-                dom.lbm_synchronize()
+                dom.lbm_step(0)   # surfaces an instability found by earlier steps
             except lbm.LBMError as e:
                 failed[jid] = str(e)
                 continue
-            if rem <= 0:
-                finished[jid] = dom.lbm_read_macroscopic()
-        for jid in list(finished) + list(failed):
+            if done is not None and done.query():
+                try:
+                    dom.lbm_synchronize()
+                    finished[jid] = dom.lbm_read_macroscopic()
+                except lbm.LBMError as e:
+                    failed[jid] = str(e)
+        gone = list(finished) + list(failed)
+        if any(j in self.batch_ids for j in gone):
+            self._drop_batch()
+        for jid in gone:
             self.doms[jid][1].close()
             del self.doms[jid]
         return finished, failed
@@ -204,7 +259,7 @@ def run_alone(spec: JobSpec):
     """The job on its own: create, init, step, read (the reference for the mix)."""
     ex = GpuExecutor()
     ex.start(spec)
-    spec_, dom, _ = ex.doms[spec.job_id]
+    dom = ex.doms[spec.job_id][1]
     try:
         dom.lbm_step(spec.steps)
         dom.lbm_synchronize()
@@ -240,7 +295,11 @@ def serve(jobs, arrivals, budget_bytes, slice_steps=200, max_slots=64, executor=
             if nxt < len(jobs):
                 time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
             continue
-        finished, failed = ex.slice(slice_steps)
+        if ex.idle():
+            time.sleep(0.0005)  # only completions to wait for
+        else:
+            ex.slice(slice_steps)
+        finished, failed = ex.poll()
         t = time.perf_counter() - t0
         for jid, res in finished.items():
             done[jid] = t - arrival_of[jid]
@@ -258,7 +317,7 @@ def serve(jobs, arrivals, budget_bytes, slice_steps=200, max_slots=64, executor=
                 p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
                 aggregate_mlups=lups_done / wall / 1e6, peak_resident_bytes=sched.peak_bytes,
                 budget_bytes=budget_bytes, admissions_while_busy=overlap_admissions,
-                failures=fail, results=results)
+                batch_builds=getattr(ex, "batch_builds", None), failures=fail, results=results)
 
 
 def _coex_pair(ex, j):
@@ -280,9 +339,7 @@ def main():
     import torch
     free, _ = torch.cuda.mem_get_info()
     jobs = random_jobs(args.jobs, args.seed, args.scale)
-    total_lups = sum(j.N * j.steps for j in jobs)
-    # ~80% load at an expected ~9 GLUPS of mixed work
-    rate = args.rate or 0.8 * len(jobs) / (total_lups / 9e9)
+    rate = args.rate or rate_for_load(jobs)
     arrivals = poisson_arrivals(len(jobs), rate, args.seed)
     rep = serve(jobs, arrivals, int(args.budget_frac * free), slice_steps=args.slice)
     rep.pop("results")

@@ -42,21 +42,34 @@ def test_scheduler_admits_by_footprint_and_slots():
 
 
 class FakeExecutor:
-    """Steps jobs instantly in slices; records how many were resident together."""
+    """Enqueues slices instantly; a job completes one poll after its last slice (as a
+    device a slice behind the host would report it); records how many were resident
+    together."""
 
     def __init__(self):
         self.doms = {}
         self.max_resident = 0
+        self.slices = 0
 
     def start(self, spec):
-        self.doms[spec.job_id] = [spec, None, spec.steps]
+        self.doms[spec.job_id] = [spec, None, spec.steps, None, None]
         self.max_resident = max(self.max_resident, len(self.doms))
 
     def slice(self, k):
+        self.slices += 1
+        for v in self.doms.values():
+            if v[2] > 0:
+                v[2] -= min(k, v[2])
+                if v[2] == 0:
+                    v[4] = self.slices
+
+    def idle(self):
+        return all(v[2] == 0 for v in self.doms.values())
+
+    def poll(self):
         finished = {}
         for jid, v in list(self.doms.items()):
-            v[2] -= min(k, v[2])
-            if v[2] <= 0:
+            if v[4] is not None and self.slices > v[4] or (v[4] is not None and self.idle()):
                 finished[jid] = ("rho", "u")
                 del self.doms[jid]
         return finished, {}
