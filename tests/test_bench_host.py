@@ -71,11 +71,13 @@ def test_gpu_arm_helpers_resolve_and_count_bytes():
     assert "D3Q27" in metric and config["nodes"] == wl.N
 
 
-def test_pass1_bytes_count_the_padded_auxiliary_writes():
+def test_pass1_bytes_count_the_padded_auxiliary_fields():
+    """Pass 1 writes (rho, psi) and j, pass 1b reads them and writes q: 2 + 3 + 2 + 3
+    + 3 = 13 float32 words per padded node, on top of the 27 population reads."""
     from paper_2201_12404_gb300 import workloads as WL
     wl = WL.by_name("drop3d")
     pn = 516 * 516 * 260  # (512 + 4, a multiple of 4) x (512 + 4) x (256 + 4)
-    assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 5 * 4
+    assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 13 * 4
 
 
 
