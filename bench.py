@@ -260,10 +260,11 @@ def recorded_traffic(key):
 # GPU arm
 # ---------------------------------------------------------------------------
 def algorithmic_bytes_k2(wl, pop_bytes, aux_bytes):
-    """Force+collide+stream kernel: each population read once and written once,
-    each auxiliary field of the node read once (halo re-reads are cache hits)."""
+    """Force+collide+stream kernel: each population read once and written once;
+    the node's D components of q and of the force F read once (the q halo re-reads
+    are cache hits)."""
     Q = 27 if wl.D == 3 else 9
-    return wl.N * (2 * Q * pop_bytes + (2 + wl.D) * aux_bytes)
+    return wl.N * (2 * Q * pop_bytes + 2 * wl.D * aux_bytes)
 
 
 def serving_sample(n_jobs, scale=0.25, seed=None):
@@ -290,12 +291,13 @@ def serving_sample(n_jobs, scale=0.25, seed=None):
 def algorithmic_bytes_k1(wl, pop_bytes, aux_bytes):
     """Passes 1 and 1b, timed together: pass 1 reads each population once and
     writes (rho, psi) and the D momentum planes j at every padded node (ghosts
-    included); pass 1b reads those 2 + D fields once per padded node (halo
-    re-reads are cache hits) and writes the D planes of q there."""
+    included); pass 1b reads the (rho, psi) pairs once per padded node (halo
+    re-reads are cache hits) and j once per interior node, writes q at every
+    padded node (the ghosts image interior nodes) and F over j at the interior."""
     Q = 27 if wl.D == 3 else 9
     px = (wl.nx + 4 + 3) // 4 * 4
     pn = px * (wl.ny + 4) * ((wl.nz + 4) if wl.D == 3 else 1)
-    return wl.N * Q * pop_bytes + pn * (2 * (2 + wl.D) + wl.D) * aux_bytes
+    return wl.N * Q * pop_bytes + pn * (2 + wl.D + 2 + wl.D) * aux_bytes + wl.N * 2 * wl.D * aux_bytes
 
 
 def run_ours(args):

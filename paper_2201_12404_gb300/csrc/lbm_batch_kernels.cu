@@ -73,14 +73,15 @@ __global__ void __launch_bounds__(BX * BY, sizeof(R) == 4 ? LBM_BATCH_MINBLOCKS_
       qflux_tile_staged<2, BX, BY, 1, R, A>(a.jobs[w.job], w.tx * BX, w.ty * BY, 0, s_aux);
     }
     if (!grid_barrier(a.barrier, a.error, a.poll_limit, a.skip_arrival)) return;
+    // pass 2: nothing staged is shared between threads (each uses its own column
+    // of s_h), so the tiles need no block barrier
     for (int it = blockIdx.x; it < a.n_k2; it += gridDim.x) {
-      __syncthreads();  // the previous tile's threads are done with s_aux and s_h
       const BatchItem w = a.k2[it];
       const DevDomain& d = a.jobs[w.job];
       if (((a.parity[w.job] + s) & 1) == 0)
-        collide_tile<2, BX, BY, 1, 0, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, s_h, nullptr, 0);
+        collide_tile<2, BX, BY, 1, 0, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, nullptr, s_h, nullptr, 0);
       else
-        collide_tile<2, BX, BY, 1, 1, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, s_aux, nullptr, s_h, nullptr, 0);
+        collide_tile<2, BX, BY, 1, 1, S, R, A, false>(d, nullptr, w.tx * BX, w.ty * BY, 0, nullptr, s_h, nullptr, 0);
     }
     if (!grid_barrier(a.barrier, a.error, a.poll_limit, a.skip_arrival)) return;
   }

@@ -1,14 +1,14 @@
 // Pass 2 of a time step: force + collide + stream, one thread per interior node.
 //
-// A block owns a tile of Blocks<D> nodes.  One thread starts a TMA bulk-tensor
-// copy of the density and the signed pseudo-potential of the tile plus a 2-node
-// halo into shared memory; while it is in flight every thread gathers its
-// populations, then waits on the copy's mbarrier (bounded).  Each thread
+// A block owns a tile of Blocks<D> nodes.  One thread starts TMA bulk-tensor
+// copies of the q planes of the tile plus a 1-node halo (2 along x) into shared
+// memory; while they are in flight every thread loads its node's force (Eq.
+// Kforce_final, physical sign, written by pass 1b) and gathers its populations,
+// then waits on the copies' mbarrier (bounded).  Each thread
 //   - gathers its Q pre-collision populations (A-A parity aware) into registers,
 //   - forms rho, j, Pi from row sums (the three populations sharing (cy, cz)),
-//   - evaluates the force of Eq. (Kforce_final) with the physical sign from the
-//     staged tile, and Phi of Eq. (correction) from q = rho u^3 (with the sign
-//     that cancels the lattice's third-moment defect),
+//   - evaluates Phi of Eq. (correction) from the staged q = rho v^3 (with the
+//     sign that cancels the lattice's third-moment defect),
 //   - builds the one-dimensional factors of f^eq (Eq. LBMeq), f* (Eq. LBMstar)
 //     and of the dual basis of the central Hermite moments (Appendix A),
 //   - pass A: h = f - f^eq - s per population, the entropic sums
@@ -184,14 +184,13 @@ template <int D, int BX, int BY, int BZ> struct Halo {
   template <typename T> static __host__ __device__ constexpr int qstride() { return (int)((QB * sizeof(T) + 127) / 128 * 128 / sizeof(T)); }
 };
 
-// Issue the TMA copies of one tile's staged fields, all completing on `bar`: the
-// (rho, psi) halo tile into s_aux and the D q_a boxes into s_q.  Called by one thread.
+// Issue the TMA copies of the D q_a boxes of one tile into s_q, all completing on
+// `bar`.  Called by one thread.
 template <int D, int BX, int BY, int BZ, typename A>
-__device__ __forceinline__ void tma_load_fields(const TileMaps* maps, Two<A>* s_aux, A* s_q, unsigned long long* bar,
-                                                int x0, int y0, int z0) {
+__device__ __forceinline__ void tma_load_q_boxes(const TileMaps* maps, A* s_q, unsigned long long* bar, int x0, int y0,
+                                                 int z0) {
   using H = Halo<D, BX, BY, BZ>;
-  mbar_arrive_expect_tx(bar, (uint32_t)(H::HN * sizeof(Two<A>) + D * H::QB * sizeof(A)));
-  tma_load_tile<D, A>(s_aux, &maps->aux, bar, x0, y0, z0);
+  mbar_arrive_expect_tx(bar, (uint32_t)(D * H::QB * sizeof(A)));
 #pragma unroll
   for (int a = 0; a < D; ++a)
     tma_load_q<D>(s_q + a * H::template qstride<A>(), &maps->q, bar, x0, y0 + 1, D == 3 ? z0 + 1 : 0, a);
@@ -265,6 +264,21 @@ __device__ __forceinline__ void row_moments(const R (&f)[Lattice<D>::Q], Two<R> 
   m.Pyz = D == 3 ? PYZ.x + PYZ.y : (R)0;
 }
 
+// The force from the node's gradient sums G = (G3[rho], G4[psi]) per axis (the
+// class-weighted link sums of stencil_force, before the common (2, 4/3)) and the
+// node's own (rho, psi) pair c: F = rho g - (2 kappa rho, (8/3) s psi) . G.
+template <int D, typename R, typename A>
+__device__ __forceinline__ void force_from_gradients(const Phys<R>& ph, R rho, const Two<A>& c, const Two<R>& GX,
+                                                     const Two<R>& GY, const Two<R>& GZ, R (&F)[3]) {
+  // s psi at the node: psi from the stencil, s from the node's density there
+  const R spsi_c = psi_sign<R>(ph, (R)c.x) * (R)c.y;
+  const Two<R> wf = two<R>((R)2 * ph.kappa * rho, (R)(8.0 / 3.0) * spsi_c);  // (kappa rho, 2 s psi) * (2, 4/3)
+  const Two<R> tx = mul2(wf, GX), ty = mul2(wf, GY), tz = mul2(wf, GZ);
+  F[0] = rho * ph.g[0] - (tx.x + tx.y);
+  F[1] = rho * ph.g[1] - (ty.x + ty.y);
+  F[2] = D == 3 ? rho * ph.g[2] - (tz.x + tz.y) : (R)0;
+}
+
 // Force of Eq. (Kforce_final) with the physical sign, plus rho g:
 // dt F = -(2 s psi G4[psi] + kappa rho G3[rho]) + rho g, from the (rho, psi) pairs
 // at(dx, dy, dz) of the node's radius-2 stencil (at(0, 0, 0) the node itself).
@@ -312,14 +326,7 @@ __device__ __forceinline__ void stencil_force(const Phys<R>& ph, R rho, const Au
   const R2 GX = fma2(both<R>(wc), DXc, fma2(both<R>(we), DXe, mul2(both<R>(wk), DXk)));
   const R2 GY = fma2(both<R>(we), YE, mul2(both<R>(wk), YK));
   const R2 GZ = fma2(both<R>(we), ZE, mul2(both<R>(wk), ZK));
-  // s psi at the node: psi from the stencil, s from the node's density there
-  const Two<A> c_aux = at(0, 0, 0);
-  const R spsi_c = psi_sign<R>(ph, (R)c_aux.x) * (R)c_aux.y;
-  const R2 wf = two<R>((R)2 * ph.kappa * rho, (R)(8.0 / 3.0) * spsi_c);  // (kappa rho, 2 s psi) * (2, 4/3)
-  const R2 tx = mul2(wf, GX), ty = mul2(wf, GY), tz = mul2(wf, GZ);
-  F[0] = rho * ph.g[0] - (tx.x + tx.y);
-  F[1] = rho * ph.g[1] - (ty.x + ty.y);
-  F[2] = D == 3 ? rho * ph.g[2] - (tz.x + tz.y) : (R)0;
+  force_from_gradients<D, R, A>(ph, rho, at(0, 0, 0), GX, GY, GZ, F);
 }
 
 // Equilibria, k/s/h split, gamma and relaxation of one node (Eq. LBGK with the
@@ -483,57 +490,47 @@ __device__ __forceinline__ void collide_relax(const DevDomain& d, const Phys<R>&
 }
 
 // One tile of pass 2 whose origin is (x0, y0, z0), run by the BX*BY*BZ threads of
-// the block.  kTma: the halo tile and the q boxes (s_q) come from TMA copies of
-// the tensor maps `maps`, completed on `bar` (phase `phase`); otherwise each warp
-// loads halo rows and q comes from global memory.
-// kStaged (with kTma): the caller has already issued this tile's halo copy and
+// the block.  kTma: the q boxes (s_q) come from TMA copies of the tensor map
+// maps->q, completed on `bar` (phase `phase`); otherwise q comes from global memory.
+// The force F of each node is the one pass 1b wrote over its momentum planes.
+// kStaged (with kTma): the caller has already issued this tile's q copies and
 // staged its populations in s_f ([i][thread], cp.async completed); once every
 // thread has read its populations the tile calls hooks.prefetch() (the next
-// tile's populations into s_f), and once the block is done with the halo tile it
-// calls hooks.aux() (the next halo copy into s_aux) after a block barrier that
+// tile's populations into s_f), and once the block is done with the q boxes it
+// calls hooks.aux() (the next tile's q copies into s_q) after a block barrier that
 // every thread of the block reaches.
-// s_aux holds the HN (rho, psi) pairs of the halo tile; s_h Q*BX*BY*BZ values of h:
-// the pair rows first (Two<R> [pair*3 + ix][thread]), then the single row.
-// Returns false when the halo copy did not arrive within the poll limit.
+// s_h holds Q*BX*BY*BZ values of h: the pair rows first (Two<R> [pair*3 +
+// ix][thread]), then the single row.
+// Returns false when the q copy did not arrive within the poll limit.
 template <int D, int BX, int BY, int BZ, int P, typename S, typename R, typename A, bool kTma,
           bool kStaged = false, typename Hooks = NoHooks>
 __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps* maps, int x0, int y0, int z0,
-                                             Two<A>* s_aux, A* s_q, R* s_h, unsigned long long* bar, uint32_t phase,
+                                             A* s_q, R* s_h, unsigned long long* bar, uint32_t phase,
                                              const S* s_f = nullptr, const Hooks& hooks = Hooks()) {
   constexpr int Q = Lattice<D>::Q;
   constexpr int NT = BX * BY * BZ;
-  constexpr int HX = Halo<D, BX, BY, BZ>::HX, HY = Halo<D, BX, BY, BZ>::HY, HZ = Halo<D, BX, BY, BZ>::HZ;
   constexpr int NP = RowPairs<D>::kPairs;
   using RP = RowPairs<D>;
   using R2 = Two<R>;
   const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
   const Phys<R>& ph = phys<R>(d);
 
-  // ---- stage (rho, psi) of the tile plus halo; padded coordinates of the halo
-  //      origin are the tile origin itself
-  if (kTma && !kStaged) {
-    // x0 is a multiple of BX (>= 32), so the box starts 16-byte aligned
-    if (tid == 0) tma_load_fields<D, BX, BY, BZ, A>(maps, s_aux, s_q, bar, x0, y0, z0);
-  } else if (!kTma) {
-    const Two<A>* a2 = (const Two<A>*)d.aux;
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int r = warp; r < HY * HZ; r += NT / 32) {
-      const int yp = y0 + r % HY, zp = z0 + r / HY;
-      const bool row_ok = yp < d.py && zp < d.pz;
-      const long long base = (long long)d.px * ((long long)yp + (long long)d.py * zp) + x0;
-      for (int hx = lane; hx < HX; hx += 32) {
-        const bool ok = row_ok && x0 + hx < d.px;
-        s_aux[r * HX + hx] = ok ? a2[base + hx] : two<A>((A)1, (A)0);
-      }
-    }
-    __syncthreads();
-  }
+  // x0 is a multiple of BX (>= 32), so the q boxes start 16-byte aligned
+  if (kTma && !kStaged && tid == 0) tma_load_q_boxes<D, BX, BY, BZ, A>(maps, s_q, bar, x0, y0, z0);
 
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + (D == 3 ? threadIdx.z : 0);
   const bool active = x < d.nx && y < d.ny && z < d.nz;
   const long long n = node_of(d, x, y, z);
   const bool fast = P == 0 || fast_links<D>(d, x, y, z);
+  const long long pc = pnode_of<D>(d, x, y, z);
 
+  // the node's force (Eq. Kforce_final), from pass 1b
+  A Fa[3] = {0, 0, 0};
+  if (active) {
+    const A* aF = (const A*)d.aux + (2 + D) * d.PN + pc;
+#pragma unroll
+    for (int a = 0; a < D; ++a) Fa[a] = aF[a * d.PN];
+  }
   R f[Q];
   if (kStaged) {
 #pragma unroll
@@ -563,10 +560,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   // every staged population has been consumed: s_f may take the next tile's
   if (kStaged) hooks.prefetch();
 
-  // ---- force from the staged (rho, psi) halo tile
-  const int sc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (D == 3 ? threadIdx.z + 2 : 0));
-  R F[3];
-  stencil_force<D, R, A>(ph, rho, [&](int dx, int dy, int dz) { return s_aux[sc + dx + HX * (dy + HY * dz)]; }, F);
+  const R F[3] = {(R)Fa[0], (R)Fa[1], (R)Fa[2]};
 
   // ---- Phi_aa = -(1 - omega/2) d_a q_a, central difference.  The sign is the one
   // that cancels the lattice's third-moment defect (sum f^eq c_a^3 = rho u_a where
@@ -585,7 +579,6 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     }
   } else {
     const A* a_q = (const A*)d.aux + 2 * d.PN;
-    const long long pc = pnode_of<D>(d, x, y, z);
     const long long sy = d.px, sz = (long long)d.px * d.py;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -595,7 +588,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     }
   }
   if (kStaged) {
-    // the block is done with the staged fields (a block-wide vote on the copy's arrival)
+    // the block is done with the q boxes (a block-wide vote on the copy's arrival)
     if (__syncthreads_or(!tile_ok)) {
       if (tid == 0) atomicOr(d.flags, 2u);
       mbar_wait_bounded(bar, phase, kTileWaitPolls);
@@ -659,10 +652,11 @@ __device__ __forceinline__ int ghost_of(int x, int n, int wlo, int whi, bool* wa
 // (x0, y0, z0), run by TX x TY threads, each walking TK nodes (along z in 3-D,
 // along y in 2-D): q_a = rho v_a^3 (Eq. (correction) with P0/rho = cs^2) with v =
 // (j + F/2)/rho the fluid velocity of the exact-difference forcing, F the force of
-// Eq. (Kforce_final) from the staged (rho, psi) halo tile s_aux (pass 2's stencil),
-// j (loaded by qflux_load_j) and rho those pass 1 wrote for the node.  The node's q
-// also goes to the ghost nodes that image it (negated across a wall: the no-slip
-// image of pass 1's fields).
+// Eq. (Kforce_final) from the staged (rho, psi) halo tile s_aux, j (loaded by
+// qflux_load_j) and rho those pass 1 wrote for the node.  The node's q also goes to
+// the ghost nodes that image it (negated across a wall: the no-slip image of pass
+// 1's fields).  F itself is written over the node's j (read by this thread alone,
+// before): pass 2 takes the force from there instead of evaluating the stencil again.
 template <int D, int TX, int TY, int TK> struct QTileShape {
   static constexpr int EY = D == 3 ? TY : TY * TK, EZ = D == 3 ? TK : 1;
   static constexpr int HX = TX + 4, HY = EY + 4, HZ = D == 3 ? EZ + 4 : 1;
@@ -683,11 +677,44 @@ __device__ __forceinline__ void qflux_load_j(const DevDomain& d, int x0, int y0,
   }
 }
 
+// q and F of one interior node to the auxiliary planes (F over the node's j), and
+// q to the ghost nodes imaging the node: every combination of its own or its ghost
+// coordinate on each axis that has a ghost, other than its own on all of them.
+template <int D, typename R, typename A>
+__device__ __forceinline__ void qflux_store(const DevDomain& d, int x, int y, int z, int gx, bool gw_x, R rho,
+                                            const A (&j)[3], const R (&F)[3]) {
+  A* aux = (A*)d.aux;
+  const long long pn = pnode_of<D>(d, x, y, z);
+  const R inv = (R)1 / rho;
+  A q[3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const R v = ((R)j[a] + (R)0.5 * F[a]) * inv;
+    q[a] = (A)(rho * v * v * v);
+    aux[(2 + a) * d.PN + pn] = q[a];
+    aux[(2 + D + a) * d.PN + pn] = (A)F[a];  // F replaces j: pass 2 reads it at the node
+  }
+  bool gw_y = false, gw_z = false;
+  const int gy = ghost_of(y, d.ny, d.wall_lo[1], d.wall_hi[1], &gw_y);
+  const int gz = D == 3 ? ghost_of(z, d.nz, d.wall_lo[2], d.wall_hi[2], &gw_z) : -1;
+  if (gx < 0 && gy < 0 && gz < 0) return;
+#pragma unroll 1
+  for (int m = 1; m < (1 << D); ++m) {
+    if (((m & 1) && gx < 0) || ((m & 2) && gy < 0) || ((m & 4) && gz < 0)) continue;
+    const int cx = (m & 1) ? gx : x + 2, cy = (m & 2) ? gy : y + 2, cz = D == 3 ? ((m & 4) ? gz : z + 2) : 0;
+    const bool flip = ((m & 1) && gw_x) || ((m & 2) && gw_y) || ((m & 4) && gw_z);
+    const long long g = (long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz);
+#pragma unroll
+    for (int a = 0; a < D; ++a) aux[(2 + a) * d.PN + g] = flip ? -q[a] : q[a];
+  }
+}
+
+// Pass 1b node by node (the 2-D kernels): each of the thread's TK nodes evaluates
+// the stencil of Eq. (Kforce_final) from the staged tile on its own.
 template <int D, int TX, int TY, int TK, typename R, typename A>
 __device__ __forceinline__ void qflux_nodes(const DevDomain& d, int x0, int y0, int z0, const Two<A>* s_aux,
                                             const A (&jn)[TK][D]) {
   using SH = QTileShape<D, TX, TY, TK>;
-  A* aux = (A*)d.aux;
   const int x = x0 + threadIdx.x;
   bool gw_x = false;
   const int gx = ghost_of(x, d.nx, d.wall_lo[0], d.wall_hi[0], &gw_x);
@@ -701,29 +728,111 @@ __device__ __forceinline__ void qflux_nodes(const DevDomain& d, int x0, int y0, 
     R F[3];
     stencil_force<D, R, A>(phys<R>(d), rho,
                            [&](int dx, int dy, int dz) { return s_aux[sc + dx + SH::HX * (dy + SH::HY * dz)]; }, F);
-    const long long pn = pnode_of<D>(d, x, y, z);
-    const R inv = (R)1 / rho;
-    A q[3];
+    const A j[3] = {jn[k][0], jn[k][1], D == 3 ? jn[k][D - 1] : (A)0};
+    qflux_store<D, R, A>(d, x, y, z, gx, gw_x, rho, j, F);
+  }
+}
+
+// Pass 1b in 3-D, plane by plane.  A thread walks the TK + 4 z planes of its column
+// of the halo tile once.  Of each plane it reads the 17 (rho, psi) pairs that the
+// radius-2 stencil of Eq. (Kforce_final) touches there (offsets in {-1, 0, 1}^2 and
+// in {-2, 0, 2}^2) and adds the plane's share of the link sums to the nodes within
+// two planes of it; a node's sums are complete, and the node is stored, once plane
+// z + 2 is in.  The sums are stencil_force's, regrouped: a link row (cy, cz) takes
+// its near points r + c from plane z + cz and its far points r + 2c from plane
+// z + 2 cz, and both enter linearly.  Shared-memory reads per node fall from 53 to
+// 17 (TK + 4) / TK.
+template <int TX, int TY, int TK, typename R, typename A>
+__device__ __forceinline__ void qflux_nodes_zwalk(const DevDomain& d, int x0, int y0, int z0, const Two<A>* s_aux) {
+  using SH = QTileShape<3, TX, TY, TK>;
+  using R2 = Two<R>;
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (!(x < d.nx && y < d.ny)) return;
+  const Phys<R>& ph = phys<R>(d);
+  bool gw_x = false;
+  const int gx = ghost_of(x, d.nx, d.wall_lo[0], d.wall_hi[0], &gw_x);
+  // class weights w_yz / 6 (centre 4/3, edge 1/3, corner 1/12, over 6), and the same
+  // times the far points' (-1/2, -1/8)
+  constexpr double wc = 4.0 / 18.0, we = 1.0 / 18.0, wk = 1.0 / 72.0;
+  const R2 Wc = both<R>((R)wc), We = both<R>((R)we), Wk = both<R>((R)wk);
+  const R2 WcF = two<R>((R)(-0.5 * wc), (R)(-0.125 * wc)), WeF = two<R>((R)(-0.5 * we), (R)(-0.125 * we));
+  const R2 WkF = two<R>((R)(-0.5 * wk), (R)(-0.125 * wk));
+  const R2 four = both<R>((R)4), zero2 = both<R>((R)0);
+  const Two<A>* col = s_aux + (threadIdx.x + 2) + SH::HX * (threadIdx.y + 2);  // this column, plane 0
+  auto P = [&](int hz, int dx, int dy) {
+    const Two<A> v = col[dx + SH::HX * (dy + SH::HY * hz)];
+    return two<R>((R)v.x, (R)v.y);
+  };
+  const long long pj = pnode_of<3>(d, x, y, z0);
+  const long long plane = (long long)d.px * d.py;
+  const A* aj = (const A*)d.aux + 5 * d.PN;  // the j planes, (2 + D) PN
+  R2 G[TK][3];
+  Two<A> c[TK];
+  A j[TK][3];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const R v = ((R)jn[k][a] + (R)0.5 * F[a]) * inv;
-      q[a] = (A)(rho * v * v * v);
-      aux[(2 + a) * d.PN + pn] = q[a];
+  for (int hz = 0; hz < TK + 4; ++hz) {
+    // node k has its centre in plane k + 2; this plane is its dz = hz - k - 2
+    if (hz < TK) {
+      // the momenta of the node whose first plane this is, four planes before use
+      const bool in = z0 + hz < d.nz;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) j[hz][a] = in ? aj[a * d.PN + pj + hz * plane] : (A)0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) G[hz][a] = zero2;
     }
-    // the ghost nodes imaging this node: every combination of its own or its ghost
-    // coordinate on each axis that has a ghost, other than its own on all of them
-    bool gw_y = false, gw_z = false;
-    const int gy = ghost_of(y, d.ny, d.wall_lo[1], d.wall_hi[1], &gw_y);
-    const int gz = D == 3 ? ghost_of(z, d.nz, d.wall_lo[2], d.wall_hi[2], &gw_z) : -1;
-    if (gx < 0 && gy < 0 && gz < 0) continue;
-#pragma unroll 1
-    for (int m = 1; m < (1 << D); ++m) {
-      if (((m & 1) && gx < 0) || ((m & 2) && gy < 0) || ((m & 4) && gz < 0)) continue;
-      const int cx = (m & 1) ? gx : x + 2, cy = (m & 2) ? gy : y + 2, cz = D == 3 ? ((m & 4) ? gz : z + 2) : 0;
-      const bool flip = ((m & 1) && gw_x) || ((m & 2) && gw_y) || ((m & 4) && gw_z);
-      const long long g = (long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz);
+    const int k_up2 = hz - 4, k_dn2 = hz, k_up1 = hz - 3, k_dn1 = hz - 1, k_c = hz - 2;
+    const bool r_up2 = k_up2 >= 0 && k_up2 < TK, r_dn2 = k_dn2 < TK, r_up1 = k_up1 >= 0 && k_up1 < TK;
+    const bool r_dn1 = k_dn1 >= 0 && k_dn1 < TK, r_c = k_c >= 0 && k_c < TK;
+    const R2 p00 = P(hz, 0, 0);
+    if (r_c) c[k_c] = col[SH::HX * SH::HY * hz];
+    if (r_up2 || r_dn2 || r_c) {
+      // far points: row sums DF = t(+2) - t(-2), UF = 4 t(0) + t(+2) + t(-2) at dy = 2 cy
+      R2 DF[3], UF[3];
 #pragma unroll
-      for (int a = 0; a < D; ++a) aux[(2 + a) * d.PN + g] = flip ? -q[a] : q[a];
+      for (int cy = -1; cy <= 1; ++cy) {
+        const R2 fm = P(hz, -2, 2 * cy), fp = P(hz, 2, 2 * cy);
+        DF[cy + 1] = sub2(fp, fm);
+        UF[cy + 1] = fma2(four, cy == 0 ? p00 : P(hz, 0, 2 * cy), add2(fp, fm));
+      }
+      if (r_up2 || r_dn2) {
+        const R2 X = fma2(WeF, DF[1], mul2(WkF, add2(DF[0], DF[2])));
+        const R2 Y = mul2(WkF, sub2(UF[2], UF[0]));
+        const R2 Z = fma2(WeF, UF[1], mul2(WkF, add2(UF[0], UF[2])));
+        if (r_up2) { G[k_up2][0] = add2(G[k_up2][0], X); G[k_up2][1] = add2(G[k_up2][1], Y); G[k_up2][2] = add2(G[k_up2][2], Z); }
+        if (r_dn2) { G[k_dn2][0] = add2(G[k_dn2][0], X); G[k_dn2][1] = add2(G[k_dn2][1], Y); G[k_dn2][2] = sub2(G[k_dn2][2], Z); }
+      }
+      if (r_c) {
+        G[k_c][0] = fma2(WcF, DF[1], fma2(WeF, add2(DF[0], DF[2]), G[k_c][0]));
+        G[k_c][1] = fma2(WeF, sub2(UF[2], UF[0]), G[k_c][1]);
+      }
+    }
+    if (r_up1 || r_dn1 || r_c) {
+      // near points: DN = t(+1) - t(-1), UN = 4 t(0) + t(+1) + t(-1) at dy = cy
+      R2 DN[3], UN[3];
+#pragma unroll
+      for (int cy = -1; cy <= 1; ++cy) {
+        const R2 nm = P(hz, -1, cy), np = P(hz, 1, cy);
+        DN[cy + 1] = sub2(np, nm);
+        UN[cy + 1] = fma2(four, cy == 0 ? p00 : P(hz, 0, cy), add2(np, nm));
+      }
+      if (r_up1 || r_dn1) {
+        const R2 X = fma2(We, DN[1], mul2(Wk, add2(DN[0], DN[2])));
+        const R2 Y = mul2(Wk, sub2(UN[2], UN[0]));
+        const R2 Z = fma2(We, UN[1], mul2(Wk, add2(UN[0], UN[2])));
+        if (r_up1) { G[k_up1][0] = add2(G[k_up1][0], X); G[k_up1][1] = add2(G[k_up1][1], Y); G[k_up1][2] = add2(G[k_up1][2], Z); }
+        if (r_dn1) { G[k_dn1][0] = add2(G[k_dn1][0], X); G[k_dn1][1] = add2(G[k_dn1][1], Y); G[k_dn1][2] = sub2(G[k_dn1][2], Z); }
+      }
+      if (r_c) {
+        G[k_c][0] = fma2(Wc, DN[1], fma2(We, add2(DN[0], DN[2]), G[k_c][0]));
+        G[k_c][1] = fma2(We, sub2(UN[2], UN[0]), G[k_c][1]);
+      }
+    }
+    // node hz - 4 has all five of its planes
+    if (r_up2 && z0 + k_up2 < d.nz) {
+      const R rho = (R)c[k_up2].x;
+      R F[3];
+      force_from_gradients<3, R, A>(ph, rho, c[k_up2], G[k_up2][0], G[k_up2][1], G[k_up2][2], F);
+      qflux_store<3, R, A>(d, x, y, z0 + k_up2, gx, gw_x, rho, j[k_up2], F);
     }
   }
 }
@@ -772,15 +881,21 @@ qflux_tile_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
     tma_load_tile<D, A>(s_aux, &maps.aux_q, bar, x0, y0, z0);
   }
   __syncthreads();
-  A jn[T::TK][D];
-  qflux_load_j<D, T::TX, T::TY, T::TK, A>(d, x0, y0, z0, jn);
-  if (!mbar_wait_bounded(bar, 0, kTileWaitPolls)) {
+  auto arrived = [&]() {
+    if (mbar_wait_bounded(bar, 0, kTileWaitPolls)) return true;
     // every thread waits, so that the block cannot retire while the copy is in flight
     if (tid == 0) atomicOr(d.flags, 2u);
     mbar_wait_bounded(bar, 0, kTileWaitPolls);
-    return;
+    return false;
+  };
+  if constexpr (D == 3) {
+    // the walk loads each node's j itself, four planes ahead of its use
+    if (arrived()) qflux_nodes_zwalk<T::TX, T::TY, T::TK, R, A>(d, x0, y0, z0, s_aux);
+  } else {
+    A jn[T::TK][D];
+    qflux_load_j<D, T::TX, T::TY, T::TK, A>(d, x0, y0, z0, jn);
+    if (arrived()) qflux_nodes<D, T::TX, T::TY, T::TK, R, A>(d, x0, y0, z0, s_aux, jn);
   }
-  qflux_nodes<D, T::TX, T::TY, T::TK, R, A>(d, x0, y0, z0, s_aux, jn);
 }
 
 // Dynamic shared memory of the pass-1b kernel: the halo tile and its mbarrier.
@@ -794,7 +909,6 @@ __global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz,
 collide_stream_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
   using H = Halo<D, BX, BY, BZ>;
-  __shared__ __align__(128) Two<A> s_aux[H::HN];                     // [z][y][x] (rho, psi)
   __shared__ __align__(128) A s_q[D * H::template qstride<A>()];     // [a][z][y][x] q_a
   __shared__ __align__(8) unsigned long long tile_bar;
   // higher-order part h_i of every node of the tile, [i][thread] (dynamic: above 48 KB in float64)
@@ -803,7 +917,7 @@ collide_stream_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
   if (tid == 0) mbar_init(&tile_bar, 1);
   __syncthreads();
   collide_tile<D, BX, BY, BZ, P, S, R, A, true>(d, &maps, blockIdx.x * BX, blockIdx.y * BY,
-                                                 D == 3 ? blockIdx.z * BZ : 0, s_aux, s_q, (R*)smem_dyn, &tile_bar, 0);
+                                                 D == 3 ? blockIdx.z * BZ : 0, s_q, (R*)smem_dyn, &tile_bar, 0);
 }
 
 // Start the copies of the pre-collision populations of node (x, y, z) into the
@@ -827,15 +941,14 @@ __device__ __forceinline__ void stage_populations(const DevDomain& d, int x, int
 // ... (x fastest).  While it computes tile t the copies of tile t + gridDim.x are in
 // flight: its populations (cp.async, started as soon as tile t's have been read
 // into registers; the A-A pattern makes that safe, since a node's read slots are
-// written by that node alone within the step) and, once the force stencil of tile t
-// is done, its halo tile (TMA).
+// written by that node alone within the step) and, once the q boxes of tile t have
+// been read, its q boxes (TMA).
 template <int D, int P, typename S, typename R, typename A>
 __global__ void __launch_bounds__(Blocks<D>::bx * Blocks<D>::by * Blocks<D>::bz, LBM_K2_MINBLOCKS(R, D))
 collide_stream_persistent_kernel(DevDomain d, const __grid_constant__ TileMaps maps, int ntx, int nty, int ntiles) {
   constexpr int BX = Blocks<D>::bx, BY = Blocks<D>::by, BZ = Blocks<D>::bz;
   constexpr int NT = BX * BY * BZ;
   using H = Halo<D, BX, BY, BZ>;
-  __shared__ __align__(128) Two<A> s_aux[H::HN];                  // [z][y][x] (rho, psi)
   __shared__ __align__(128) A s_q[D * H::template qstride<A>()];  // [a][z][y][x] q_a
   __shared__ __align__(8) unsigned long long tile_bar;
   extern __shared__ __align__(16) unsigned char smem_dyn[];
@@ -855,7 +968,7 @@ collide_stream_persistent_kernel(DevDomain d, const __grid_constant__ TileMaps m
   origin(t, x0, y0, z0);
   stage_populations<D, P, S, NT>(d, x0 + threadIdx.x, y0 + threadIdx.y, z0 + threadIdx.z, s_f, tid);
   cp_async_commit();
-  if (tid == 0) tma_load_fields<D, BX, BY, BZ, A>(&maps, s_aux, s_q, &tile_bar, x0, y0, z0);
+  if (tid == 0) tma_load_q_boxes<D, BX, BY, BZ, A>(&maps, s_q, &tile_bar, x0, y0, z0);
   for (uint32_t it = 0;; ++it) {
     const int tn = t + (int)gridDim.x;
     int nx0 = 0, ny0 = 0, nz0 = 0;
@@ -863,7 +976,6 @@ collide_stream_persistent_kernel(DevDomain d, const __grid_constant__ TileMaps m
     struct Next {
       const DevDomain& d;
       const TileMaps* maps;
-      Two<A>* s_aux;
       A* s_q;
       unsigned long long* bar;
       S* s_f;
@@ -876,12 +988,12 @@ collide_stream_persistent_kernel(DevDomain d, const __grid_constant__ TileMaps m
       __device__ void aux() const {
         if (valid && tid == 0) {
           fence_proxy_async_smem();
-          tma_load_fields<D, BX, BY, BZ, A>(maps, s_aux, s_q, bar, x0, y0, z0);
+          tma_load_q_boxes<D, BX, BY, BZ, A>(maps, s_q, bar, x0, y0, z0);
         }
       }
-    } next{d, &maps, s_aux, s_q, &tile_bar, s_f, tid, nx0, ny0, nz0, tn < ntiles};
+    } next{d, &maps, s_q, &tile_bar, s_f, tid, nx0, ny0, nz0, tn < ntiles};
     cp_async_wait_all();  // this thread's populations of tile t are in s_f
-    if (!collide_tile<D, BX, BY, BZ, P, S, R, A, true, true, Next>(d, &maps, x0, y0, z0, s_aux, s_q, s_h, &tile_bar,
+    if (!collide_tile<D, BX, BY, BZ, P, S, R, A, true, true, Next>(d, &maps, x0, y0, z0, s_q, s_h, &tile_bar,
                                                                      it & 1u, s_f, next))
       break;
     if (tn >= ntiles) break;

@@ -4,10 +4,12 @@
 // Data layout in HBM (one domain):
 //   populations  f[i * N + node]          SoA, node = x + nx*(y + ny*z), one A-A buffer
 //   auxiliary    aux2[pnode] = (rho, psi) interleaved pairs, then q_a[pnode] planes
-//                                         (element offset (2 + a) * PN), then the bare
-//                                         momentum j_a[pnode] (offset (2 + D + a) * PN);
-//                                         padded by a 2-node ghost layer on every axis
-//                                         (2-D: z not padded)
+//                                         (element offset (2 + a) * PN), then D planes
+//                                         at offset (2 + D + a) * PN that hold the bare
+//                                         momentum j_a after pass 1 and the force F_a
+//                                         after pass 1b (interior nodes); padded by a
+//                                         2-node ghost layer on every axis (2-D: z not
+//                                         padded)
 // The A-A pattern keeps one population buffer: an even step (parity 0) reads and
 // writes the node's own slots (writing direction i into slot Q-1-i), an odd step
 // (parity 1) reads the neighbours' slots and writes back into them, so that after
@@ -37,7 +39,7 @@ template <int D> __host__ __device__ constexpr double wq(int i) {
 }
 
 // Block shape of the per-node kernels (x fastest); the force+collide+stream pass
-// stages a tile of this shape plus a 2-node halo of the auxiliary fields.
+// stages the q planes of a tile of this shape plus a 1-node halo (2 along x).
 template <int D> struct Blocks;
 template <> struct Blocks<2> { static constexpr int bx = 64, by = 4, bz = 1; };
 template <> struct Blocks<3> { static constexpr int bx = 32, by = 4, bz = 2; };
@@ -112,7 +114,6 @@ struct DevDomain {
 
 // The tensor maps of the collide kernel's TMA loads (passed as a kernel parameter).
 struct TileMaps {
-  CUtensorMap aux;    // (rho, psi) halo tile of pass 2
   CUtensorMap q;      // q_a boxes of pass 2
   CUtensorMap aux_q;  // (rho, psi) halo tile of pass 1b (QTile)
 };
@@ -121,10 +122,15 @@ struct TileMaps {
 // nodes along z (tile TX x TY x TK), in 2-D along y (tile TX x TY*TK).  Taller
 // tiles than pass 2's keep the staged halo small against the tile: pass 1b does
 // little arithmetic per node, so the halo traffic would dominate.  kPairBytes is
-// the size of one staged (rho, psi) pair.
+// the size of one staged (rho, psi) pair.  In float32 3-D, TK = 4 and TK = 8 run
+// alike on the 512x512x256 impact (pass 1 + 1b 2.27 and 2.29 ms); 4 holds 76
+// registers and a 28 KB tile against 126 and 41 KB.
+#ifndef LBM_QTILE_TK3_F32
+#define LBM_QTILE_TK3_F32 4
+#endif
 template <int D, int kPairBytes> struct QTile {
   static constexpr int TX = D == 3 ? 32 : 64, TY = D == 3 ? 8 : 4;
-  static constexpr int TK = D == 3 ? (kPairBytes == 8 ? 8 : 4) : 4;
+  static constexpr int TK = D == 3 ? (kPairBytes == 8 ? LBM_QTILE_TK3_F32 : 4) : 4;
   static constexpr int EX = TX, EY = D == 3 ? TY : TY * TK, EZ = D == 3 ? TK : 1;  // tile extents
   static constexpr int HX = EX + 4, HY = EY + 4, HZ = D == 3 ? EZ + 4 : 1;         // with the halo
   static constexpr int HN = HX * HY * HZ;

@@ -4,11 +4,12 @@
 //  moments_eos_kernel    (pass 1)  gather f, form rho and j, evaluate the
 //                                  Peng-Robinson pseudo-potential; writes (rho, psi) and
 //                                  j to the padded auxiliary fields, ghosts included.
-//  qflux_tile_kernel     (pass 1b) q = rho v^3, v = (j + F/2)/rho the fluid velocity,
-//                                  F from the (rho, psi) halo tile (Eq. Kforce_final),
-//                                  written to the node and the ghosts imaging it.
-//  collide_stream_kernel (pass 2)  gather f, force from the auxiliary halo
-//                                  (Eq. Kforce_final), Phi (Eq. correction), f^eq and
+//  qflux_tile_kernel     (pass 1b) F from the (rho, psi) halo tile (Eq. Kforce_final)
+//                                  and q = rho v^3, v = (j + F/2)/rho the fluid
+//                                  velocity; q to the node and the ghosts imaging it,
+//                                  F over the node's j.
+//  collide_stream_kernel (pass 2)  gather f, the node's F from pass 1b, Phi from the
+//                                  staged q boxes (Eq. correction), f^eq and
 //                                  f* (Eqs. LBMeq, LBMstar), k/s/h split (Appendix A),
 //                                  gamma (Sec. 2.4), relaxation (Eq. LBGK), A-A write.
 #pragma once

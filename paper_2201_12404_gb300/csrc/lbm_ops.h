@@ -191,18 +191,14 @@ inline void qtile_box(cuuint32_t box[3]) {
 }
 
 inline bool make_tile_maps(TileMaps* m, const DevDomain& d, int D, size_t elem_bytes, const char** why) {
-  // pass 2: a tile of Blocks<D> nodes with a 2-node halo
-  const cuuint32_t tile[3] = {D == 3 ? (cuuint32_t)Blocks<3>::bx + 4 : (cuuint32_t)Blocks<2>::bx + 4,
-                              D == 3 ? (cuuint32_t)Blocks<3>::by + 4 : (cuuint32_t)Blocks<2>::by + 4,
-                              (cuuint32_t)Blocks<3>::bz + 4};
+  // pass 1b: a QTile tile with a 2-node halo
   cuuint32_t qbox[3];
   if (D == 3) {
     if (elem_bytes == 4) qtile_box<3, 8>(qbox); else qtile_box<3, 16>(qbox);
   } else {
     if (elem_bytes == 4) qtile_box<2, 8>(qbox); else qtile_box<2, 16>(qbox);
   }
-  return make_aux_map(&m->aux, d, D, elem_bytes, tile, why) && make_aux_map(&m->aux_q, d, D, elem_bytes, qbox, why) &&
-         make_q_map(&m->q, d, D, elem_bytes, why);
+  return make_aux_map(&m->aux_q, d, D, elem_bytes, qbox, why) && make_q_map(&m->q, d, D, elem_bytes, why);
 }
 
 // Final fixed-order reduction of the diagnostic partial sums (lbm_d2q9.cu).

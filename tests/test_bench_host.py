@@ -56,13 +56,13 @@ def test_reference_arm_only_rank0_works(monkeypatch, capsys):
 
 def test_gpu_arm_helpers_resolve_and_count_bytes():
     """The helpers the GPU arm calls exist and give the per-launch byte counts
-    the roofline line reports (236 B per node for FP32 D3Q27)."""
+    the roofline line reports (240 B per node for FP32 D3Q27)."""
     from paper_2201_12404_gb300 import workloads as WL
     wl = WL.by_name("drop3d")
-    assert bench.algorithmic_bytes_k2(wl, 4, 4) == 236 * wl.N
-    assert bench.algorithmic_bytes_k2(wl, 8, 8) == 472 * wl.N
+    assert bench.algorithmic_bytes_k2(wl, 4, 4) == 240 * wl.N
+    assert bench.algorithmic_bytes_k2(wl, 8, 8) == 480 * wl.N
     t = bench.recorded_traffic("d3q27_fp32_collide_stream")
-    assert t is None or 0.8 * 236 * wl.N < t < 1.5 * 236 * wl.N
+    assert t is None or 0.8 * 240 * wl.N < t < 1.5 * 240 * wl.N
     assert bench.recorded_traffic("no such kernel") is None
 
     class Args:
@@ -72,12 +72,14 @@ def test_gpu_arm_helpers_resolve_and_count_bytes():
 
 
 def test_pass1_bytes_count_the_padded_auxiliary_fields():
-    """Pass 1 writes (rho, psi) and j, pass 1b reads them and writes q: 2 + 3 + 2 + 3
-    + 3 = 13 float32 words per padded node, on top of the 27 population reads."""
+    """Pass 1 writes (rho, psi) and j at every padded node; pass 1b reads the pairs
+    there and writes q there (2 + 3 + 2 + 3 = 10 float32 words per padded node),
+    and reads j and writes F at the interior (6 words per node), on top of the 27
+    population reads."""
     from paper_2201_12404_gb300 import workloads as WL
     wl = WL.by_name("drop3d")
     pn = 516 * 516 * 260  # (512 + 4, a multiple of 4) x (512 + 4) x (256 + 4)
-    assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 13 * 4
+    assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 10 * 4 + wl.N * 6 * 4
 
 
 
