@@ -289,15 +289,15 @@ def serving_sample(n_jobs, scale=0.25, seed=None):
 
 
 def algorithmic_bytes_k1(wl, pop_bytes, aux_bytes):
-    """Passes 1 and 1b, timed together: pass 1 reads each population once and
-    writes (rho, psi) and the D momentum planes j at every padded node (ghosts
-    included); pass 1b reads the (rho, psi) pairs once per padded node (halo
-    re-reads are cache hits) and j once per interior node, writes q at every
-    padded node (the ghosts image interior nodes) and F over j at the interior."""
+    """Passes 1 and 1b, timed together: pass 1 reads each population once, writes
+    the (rho, psi) pair at every padded node (interior nodes and the ghosts imaging
+    them) and the D momentum planes j at the interior; pass 1b reads the pairs once
+    per padded node (halo re-reads are cache hits) and j once per interior node,
+    writes q at every padded node and F over j at the interior."""
     Q = 27 if wl.D == 3 else 9
     px = (wl.nx + 4 + 3) // 4 * 4
     pn = px * (wl.ny + 4) * ((wl.nz + 4) if wl.D == 3 else 1)
-    return wl.N * Q * pop_bytes + pn * (2 + wl.D + 2 + wl.D) * aux_bytes + wl.N * 2 * wl.D * aux_bytes
+    return wl.N * Q * pop_bytes + pn * (2 + 2 + wl.D) * aux_bytes + wl.N * 3 * wl.D * aux_bytes
 
 
 def run_ours(args):

@@ -30,9 +30,9 @@ struct lbm_batch {
   // device buffers
   DevDomain* d_jobs = nullptr;
   int* d_parity = nullptr;
-  BatchItem* d_items = nullptr;  // k1 items then k2 items
+  BatchItem* d_items = nullptr;  // the tiles of every job's interior
   unsigned int* d_sync = nullptr;  // [0] arrivals, [1] generation, [2] error word
-  int n_k1 = 0, n_k2 = 0, grid = 0;
+  int n_k2 = 0, grid = 0;
   std::map<int64_t, cudaGraphExec_t> graphs;
   bool use_graph = true;
   unsigned int poll_limit = lbm::kBarrierPollsDefault;
@@ -60,16 +60,12 @@ lbm_status bfail(lbm_batch* b, lbm_status st, const std::string& msg) {
                    std::string(#call) + ": " + cudaGetErrorString(e_));                                 \
   } while (0)
 
-// Work lists of a tile shape: pass-1 tiles cover every job's padded extent
-// (nx + 4) x (ny + 4), pass-2 tiles every job's interior.
-void build_items(const std::vector<lbm_domain*>& doms, int bx, int by, std::vector<BatchItem>& k1,
-                 std::vector<BatchItem>& k2) {
-  k1.clear();
+// Work list of a tile shape: the tiles of every job's interior (each pass walks
+// them; pass 1 writes the ghost images of its nodes itself).
+void build_items(const std::vector<lbm_domain*>& doms, int bx, int by, std::vector<BatchItem>& k2) {
   k2.clear();
   for (int j = 0; j < (int)doms.size(); ++j) {
     const DevDomain& d = doms[j]->dev;
-    for (int ty = 0; ty < (d.py + by - 1) / by; ++ty)
-      for (int tx = 0; tx < (d.nx + 4 + bx - 1) / bx; ++tx) k1.push_back({j, tx, ty});
     for (int ty = 0; ty < (d.ny + by - 1) / by; ++ty)
       for (int tx = 0; tx < (d.nx + bx - 1) / bx; ++tx) k2.push_back({j, tx, ty});
   }
@@ -78,13 +74,11 @@ void build_items(const std::vector<lbm_domain*>& doms, int bx, int by, std::vect
 // Upload the work lists of variant v and size the cooperative grid.
 lbm_status select_variant(lbm_batch* b, int v) {
   const BatchVariant& var = b->variants[v];
-  std::vector<BatchItem> k1, k2;
-  build_items(b->doms, var.bx, var.by, k1, k2);
+  std::vector<BatchItem> k2;
+  build_items(b->doms, var.bx, var.by, k2);
   if (b->d_items) { cudaFree(b->d_items); b->d_items = nullptr; }
-  B_CUDA(b, cudaMalloc(&b->d_items, (k1.size() + k2.size()) * sizeof(BatchItem)));
-  B_CUDA(b, cudaMemcpy(b->d_items, k1.data(), k1.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
-  B_CUDA(b, cudaMemcpy(b->d_items + k1.size(), k2.data(), k2.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
-  b->n_k1 = (int)k1.size();
+  B_CUDA(b, cudaMalloc(&b->d_items, k2.size() * sizeof(BatchItem)));
+  B_CUDA(b, cudaMemcpy(b->d_items, k2.data(), k2.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
   b->n_k2 = (int)k2.size();
   int dev = 0, sms = 0, per_sm = 0;
   B_CUDA(b, cudaGetDevice(&dev));
@@ -92,7 +86,7 @@ lbm_status select_variant(lbm_batch* b, int v) {
   B_CUDA(b, cudaFuncSetAttribute(var.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)var.dyn_smem));
   B_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, var.kernel, var.bx * var.by, var.dyn_smem));
   if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "the batch kernel cannot be resident on an SM");
-  b->grid = std::max(1, std::min(per_sm * sms, std::max(b->n_k1, b->n_k2)));
+  b->grid = std::max(1, std::min(per_sm * sms, b->n_k2));
   b->chosen = v;
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
@@ -104,9 +98,7 @@ BatchArgs make_args(lbm_batch* b, const DevDomain* jobs, int* parity, int nsteps
   a.jobs = jobs;
   a.parity = parity;
   a.njobs = (int)b->doms.size();
-  a.k1 = b->d_items;
-  a.n_k1 = b->n_k1;
-  a.k2 = b->d_items + b->n_k1;
+  a.k2 = b->d_items;
   a.n_k2 = b->n_k2;
   a.barrier = b->d_sync;
   a.error = b->d_sync + 2;

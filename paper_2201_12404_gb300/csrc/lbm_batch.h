@@ -17,9 +17,7 @@ struct BatchArgs {
   const DevDomain* jobs;  // device array, one per job
   int* parity;            // device array: A-A parity of every job; flipped by the kernel at the end
   int njobs;
-  const BatchItem* k1;    // pass-1 tiles over the padded auxiliary extent of every job
-  int n_k1;
-  const BatchItem* k2;    // pass-2 tiles over the interior of every job
+  const BatchItem* k2;    // tiles over the interior of every job (all three passes)
   int n_k2;
   unsigned int* barrier;  // [0] arrivals, [1] generation
   unsigned int* error;    // bit 1: a bounded grid-barrier wait gave up

@@ -1,9 +1,9 @@
 // Persistent kernel that advances a batch of D2Q9 domains of uneven sizes by
-// nsteps time steps in one launch.  The blocks of a cooperative launch walk a
-// work list of pass-1 tiles (every job's padded auxiliary extent), meet at a grid
-// barrier, walk the pass-2 tiles (every job's interior), meet again, and repeat
-// for the next step.  The per-tile work is the same code as the single-domain
-// kernels (moments_eos_node, collide_tile), with the halo tile staged by warps.
+// nsteps time steps in one launch.  The blocks of a cooperative launch walk the
+// work list of tiles (every job's interior) three times per step, for pass 1,
+// pass 1b and pass 2, with a grid barrier after each.  The per-tile work is the
+// same code as the single-domain kernels (moments_eos_node, qflux_tile_staged,
+// collide_tile), with pass 1b's halo tile staged by warps.
 #include "../../include/lbm.h"
 #include "lbm_batch.h"
 #include "lbm_kernels.cuh"
@@ -58,12 +58,13 @@ __global__ void __launch_bounds__(BX * BY, sizeof(R) == 4 ? LBM_BATCH_MINBLOCKS_
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   R* s_h = (R*)smem_dyn;
   for (int s = 0; s < a.nsteps; ++s) {
-    for (int it = blockIdx.x; it < a.n_k1; it += gridDim.x) {
-      const BatchItem w = a.k1[it];
+    // pass 1 over the interior tiles (each node also writes its ghost images)
+    for (int it = blockIdx.x; it < a.n_k2; it += gridDim.x) {
+      const BatchItem w = a.k2[it];
       const DevDomain& d = a.jobs[w.job];
-      const int xp = w.tx * BX + threadIdx.x, yp = w.ty * BY + threadIdx.y;
-      if (((a.parity[w.job] + s) & 1) == 0) moments_eos_node<2, 0, S, R, A>(d, xp, yp, 0);
-      else moments_eos_node<2, 1, S, R, A>(d, xp, yp, 0);
+      const int x = w.tx * BX + threadIdx.x, y = w.ty * BY + threadIdx.y;
+      if (((a.parity[w.job] + s) & 1) == 0) moments_eos_node<2, 0, S, R, A>(d, x, y, 0);
+      else moments_eos_node<2, 1, S, R, A>(d, x, y, 0);
     }
     if (!grid_barrier(a.barrier, a.error, a.poll_limit, a.skip_arrival)) return;
     // pass 1b: q over the interior tiles (and the ghosts imaging them)

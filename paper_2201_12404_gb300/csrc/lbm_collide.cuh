@@ -631,23 +631,6 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   return true;
 }
 
-// Padded coordinate of the ghost node that images interior coordinate x along an
-// axis of n >= 5 nodes, or -1 when no ghost does (x more than 1 node from both
-// faces); *wall is set when that ghost mirrors x across a bounce-back wall.  The
-// ghost layers are 2 nodes wide: a periodic ghost sits n nodes away, a wall ghost
-// is the mirror image across the half-way wall (the inverse of ghost_image).
-__device__ __forceinline__ int ghost_of(int x, int n, int wlo, int whi, bool* wall) {
-  if (x <= 1) {
-    if (wlo) { *wall = true; return 1 - x; }
-    return x + n + 2;
-  }
-  if (x >= n - 2) {
-    if (whi) { *wall = true; return 2 * n + 1 - x; }
-    return x - n + 2;
-  }
-  return -1;
-}
-
 // Pass 1b on one tile of interior nodes of extents EX x EY x EZ whose origin is
 // (x0, y0, z0), run by TX x TY threads, each walking TK nodes (along z in 3-D,
 // along y in 2-D): q_a = rho v_a^3 (Eq. (correction) with P0/rho = cs^2) with v =

@@ -174,6 +174,23 @@ __device__ __forceinline__ bool fast_links(const DevDomain& d, int x, int y, int
          ((x >= 1 && x <= d.nx - 2) || (d.wall_lo[0] == 0 && d.wall_hi[0] == 0));
 }
 
+// Padded coordinate of the ghost node that images interior coordinate x along an
+// axis of n >= 5 nodes, or -1 when no ghost does (x more than 1 node from both
+// faces); *wall is set when that ghost mirrors x across a bounce-back wall.  The
+// ghost layers are 2 nodes wide: a periodic ghost sits n nodes away, a wall ghost
+// is the mirror image across the half-way wall (the inverse of ghost_image).
+__device__ __forceinline__ int ghost_of(int x, int n, int wlo, int whi, bool* wall) {
+  if (x <= 1) {
+    if (wlo) { *wall = true; return 1 - x; }
+    return x + n + 2;
+  }
+  if (x >= n - 2) {
+    if (whi) { *wall = true; return 2 * n + 1 - x; }
+    return x - n + 2;
+  }
+  return -1;
+}
+
 // Node index n of (x, y, z) corrected for the periodic x wrap of the neighbour
 // r - c along x: b[c + 1], c = -1, 0, +1 (used by fast_links nodes only), and the
 // byte address of slot 0 of each in the population array (elements of S).

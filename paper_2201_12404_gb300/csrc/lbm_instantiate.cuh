@@ -15,9 +15,8 @@ struct Launch {
   }
   static void moments_eos(const DevDomain& d, int parity, cudaStream_t s) {
     dim3 blk(Blocks<D>::bx, Blocks<D>::by, Blocks<D>::bz);
-    dim3 grd((d.px + blk.x - 1) / blk.x, (d.py + blk.y - 1) / blk.y, (d.pz + blk.z - 1) / blk.z);
-    if (parity == 0) moments_eos_kernel<D, 0, S, R, A><<<grd, blk, 0, s>>>(d);
-    else moments_eos_kernel<D, 1, S, R, A><<<grd, blk, 0, s>>>(d);
+    if (parity == 0) moments_eos_kernel<D, 0, S, R, A><<<node_grid(d), blk, 0, s>>>(d);
+    else moments_eos_kernel<D, 1, S, R, A><<<node_grid(d), blk, 0, s>>>(d);
   }
   static void qflux(const DevDomain& d, const TileMaps& maps, cudaStream_t s) {
     using T = QTile<D, 2 * sizeof(A)>;

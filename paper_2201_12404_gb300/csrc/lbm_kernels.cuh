@@ -19,9 +19,8 @@
 namespace lbm {
 
 // ---------------------------------------------------------------------------
-// Pass 1: one thread per padded auxiliary node.  A ghost node evaluates the
-// interior node it images (periodic wrap or mirror across a half-way wall);
-// q is negated across a wall (no-slip image).
+// Pass 1: one thread per interior node; the node also writes the ghost nodes
+// that image it (periodic wrap or mirror across a half-way wall).
 // ---------------------------------------------------------------------------
 // Interior coordinate that padded coordinate cp (ghost layers of 2) images along
 // an axis of n nodes: periodic wrap, or the mirror across a half-way wall (which
@@ -33,15 +32,17 @@ __device__ __forceinline__ int ghost_image(int cp, int n, int wlo, int whi, bool
   return t;
 }
 
+// Pass 1 at interior node (x, y, z): rho and j from the gathered populations, psi
+// from the Peng-Robinson pressure.  The (rho, psi) pair goes to the node's padded
+// position and to every ghost node imaging it (each combination of its own or its
+// ghost coordinate on the axes that have one), so that the later passes index
+// their stencils without wrap logic; j goes to the node alone (pass 1b reads it
+// there).  A warp is one aligned x row of 32 interior nodes, so each of its 27
+// population loads is one 128-byte line.
 template <int D, int P, typename S, typename R, typename A>
-__device__ __forceinline__ void moments_eos_node(const DevDomain& d, int xp, int yp, int zp) {
+__device__ __forceinline__ void moments_eos_node(const DevDomain& d, int x, int y, int z) {
   constexpr int Q = Lattice<D>::Q;
-  if (xp >= d.nx + 4 || yp >= d.py || zp >= d.pz) return;
-  bool flip = false;
-  const int x = ghost_image(xp, d.nx, d.wall_lo[0], d.wall_hi[0], &flip);
-  const int y = ghost_image(yp, d.ny, d.wall_lo[1], d.wall_hi[1], &flip);
-  const int z = D == 3 ? ghost_image(zp, d.nz, d.wall_lo[2], d.wall_hi[2], &flip) : 0;
-
+  if (x >= d.nx || y >= d.ny || z >= d.nz) return;
   R f[Q];
   gather<D, P, S, R>(d, x, y, z, f);
   R rho, j[3], Pi[6];
@@ -49,11 +50,23 @@ __device__ __forceinline__ void moments_eos_node(const DevDomain& d, int xp, int
   if (!(rho > (R)0) || !(rho < (R)INFINITY)) atomicOr(d.flags, 1u);
 
   A* aux = (A*)d.aux;
-  const long long pn = (long long)xp + (long long)d.px * ((long long)yp + (long long)d.py * (long long)zp);
-  ((Two<A>*)aux)[pn] = two<A>((A)rho, (A)psi_of<R>(d, rho));
-  // the bare momentum j of the imaged node, for the q of the next kernel
+  Two<A>* a2 = (Two<A>*)d.aux;
+  const long long pn = pnode_of<D>(d, x, y, z);
+  const Two<A> pair = two<A>((A)rho, (A)psi_of<R>(d, rho));
+  a2[pn] = pair;
 #pragma unroll
   for (int a = 0; a < D; ++a) aux[(2 + D + a) * d.PN + pn] = (A)j[a];
+  bool wall = false;
+  const int gx = ghost_of(x, d.nx, d.wall_lo[0], d.wall_hi[0], &wall);
+  const int gy = ghost_of(y, d.ny, d.wall_lo[1], d.wall_hi[1], &wall);
+  const int gz = D == 3 ? ghost_of(z, d.nz, d.wall_lo[2], d.wall_hi[2], &wall) : -1;
+  if (gx < 0 && gy < 0 && gz < 0) return;
+#pragma unroll 1
+  for (int m = 1; m < (1 << D); ++m) {
+    if (((m & 1) && gx < 0) || ((m & 2) && gy < 0) || ((m & 4) && gz < 0)) continue;
+    const int cx = (m & 1) ? gx : x + 2, cy = (m & 2) ? gy : y + 2, cz = D == 3 ? ((m & 4) ? gz : z + 2) : 0;
+    a2[(long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz)] = pair;
+  }
 }
 
 // The (rho, psi) pairs of every padded node straight from a density field

@@ -72,14 +72,14 @@ def test_gpu_arm_helpers_resolve_and_count_bytes():
 
 
 def test_pass1_bytes_count_the_padded_auxiliary_fields():
-    """Pass 1 writes (rho, psi) and j at every padded node; pass 1b reads the pairs
-    there and writes q there (2 + 3 + 2 + 3 = 10 float32 words per padded node),
-    and reads j and writes F at the interior (6 words per node), on top of the 27
-    population reads."""
+    """Pass 1 writes (rho, psi) at every padded node and j at the interior; pass 1b
+    reads the pairs and writes q at every padded node (2 + 2 + 3 = 7 float32 words
+    per padded node), reads j and writes F at the interior (with pass 1's j, 9 words
+    per interior node), on top of the 27 population reads."""
     from paper_2201_12404_gb300 import workloads as WL
     wl = WL.by_name("drop3d")
     pn = 516 * 516 * 260  # (512 + 4, a multiple of 4) x (512 + 4) x (256 + 4)
-    assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 10 * 4 + wl.N * 6 * 4
+    assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 7 * 4 + wl.N * 9 * 4
 
 
 
