@@ -849,8 +849,17 @@ __device__ __forceinline__ void qflux_tile_staged(const DevDomain& d, int x0, in
 // 41 KB buffers leave two blocks per SM, and the stencil's shared-memory reads,
 // not the copy latency, set the pace.)  A wait that gives up sets bit 1 of the
 // error word; the block then waits (bounded) for the copy and stops.
+// Resident blocks per SM asked of the register allocator for pass 1b in float32:
+// three (80 registers, 8 bytes spilled in the 3-D walk of TK = 8; float64 takes
+// what it needs, 84).  On the 512x512x256
+// impact, passes 1 + 1b take 2.10 ms so, against 2.34 ms with TK = 4 at 76
+// registers, 2.18 ms with TK = 4 at 64 and 2.21 ms with TK = 8 at 64 (spills).
+#ifndef LBM_QFLUX_MINBLOCKS
+#define LBM_QFLUX_MINBLOCKS 3
+#endif
 template <int D, typename R, typename A>
-__global__ void __launch_bounds__(QTile<D, 2 * sizeof(A)>::TX * QTile<D, 2 * sizeof(A)>::TY)
+__global__ void __launch_bounds__(QTile<D, 2 * sizeof(A)>::TX * QTile<D, 2 * sizeof(A)>::TY,
+                                  sizeof(A) == 4 ? LBM_QFLUX_MINBLOCKS : 1)
 qflux_tile_kernel(DevDomain d, const __grid_constant__ TileMaps maps) {
   using T = QTile<D, 2 * sizeof(A)>;
   extern __shared__ __align__(128) unsigned char smem_dyn[];

@@ -122,11 +122,10 @@ struct TileMaps {
 // nodes along z (tile TX x TY x TK), in 2-D along y (tile TX x TY*TK).  Taller
 // tiles than pass 2's keep the staged halo small against the tile: pass 1b does
 // little arithmetic per node, so the halo traffic would dominate.  kPairBytes is
-// the size of one staged (rho, psi) pair.  In float32 3-D, TK = 4 and TK = 8 run
-// alike on the 512x512x256 impact (pass 1 + 1b 2.27 and 2.29 ms); 4 holds 76
-// registers and a 28 KB tile against 126 and 41 KB.
+// the size of one staged (rho, psi) pair.  In float32 3-D, TK = 8: a 41 KB tile,
+// three blocks per SM (see LBM_QFLUX_MINBLOCKS).
 #ifndef LBM_QTILE_TK3_F32
-#define LBM_QTILE_TK3_F32 4
+#define LBM_QTILE_TK3_F32 8
 #endif
 template <int D, int kPairBytes> struct QTile {
   static constexpr int TX = D == 3 ? 32 : 64, TY = D == 3 ? 8 : 4;

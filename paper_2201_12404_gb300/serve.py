@@ -177,8 +177,9 @@ class GpuExecutor:
         p = spec.params(rv=rv, rl=rl)
         p.stream = stream.cuda_stream
         dom = lbm.Domain(p)
-        rho, u = WL.initial_fields(wl, rv, rl)
-        dom.lbm_init_fields(rho, u)
+        # the geometry of WL.initial_fields, built on the GPU: no host fields to
+        # compute or copy while other jobs wait for their next slice
+        dom.lbm_init_drop_on_film(wl.R, wl.film * wl.R, 2.0 * wl.W, wl.U, wl.W)
         self.doms[spec.job_id] = [spec, dom, spec.steps, stream, None]
 
     def _drop_batch(self):
