@@ -1,9 +1,10 @@
-"""Benchmark of the fused entropic-MRT two-phase lattice Boltzmann step.
+"""Benchmark of the entropic-MRT two-phase lattice Boltzmann time step.
 
 Workload: D3Q27 drop impact on a thin film, 512x512x256 nodes, FP32 populations
 in one A-A buffer (7.25 GB, far larger than the 129 MB L2, so no flush is
 needed between steps), density ratio ~1000 (T/Tc = 0.59).  One benchmark step is
-one lattice time step (both passes) over the whole domain.
+one lattice time step (its three kernels: moments and EOS, force and q, collide
+and stream) over the whole domain.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -13,7 +14,7 @@ copied in, K steps, density and velocity copied out); roofline = the
 force+collide+stream kernel's algorithmic bytes per launch over its CUDA-event
 duration, against the measured HBM copy bandwidth; cpu_baseline = the FP64
 oracle on a bounded crop of the same workload on the host cores; serving (N = 1)
-= p50/p99 latency and aggregate MLUPS of a short continuous-batching run.
+= p50/p99 latency and aggregate MLUPS of a 200-job continuous-batching run.
 
 --impl reference times the FP64 CPU oracle (the reference implementation of
 the method) on a bounded crop of the same workload; N > 1: rank 0 only.
@@ -201,7 +202,7 @@ def metric_and_config(args, wl, world):
     """Metric name and config of a benchmark line (shared by both arms)."""
     pop_bytes = {"fp64": 8, "fp32": 4, "fp16dev": 2}[args.precision]
     Q = 27 if wl.D == 3 else 9
-    metric = f"{lattice_of(wl)} entropic-MRT MLUPS (fused two-pass step, {args.precision.upper()} A-A)"
+    metric = f"{lattice_of(wl)} entropic-MRT MLUPS (whole time step, {args.precision.upper()} A-A)"
     config = {"workload": wl.name, "nodes": wl.N, "lattice": lattice_of(wl), "storage": f"{args.precision} A-A",
               "l2": l2_note(Q * pop_bytes * wl.N),
               "parallelism": f"replicas{world}" if world > 1 else "single GPU"}
