@@ -55,7 +55,10 @@ typedef enum {
   LBM_ERR_CUDA = 3,        /* a CUDA call failed */
   LBM_ERR_UNSTABLE = 4,    /* a non-finite or non-positive density appeared */
   LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait (a shared-memory tile copy) gave up */
-  LBM_ERR_STATE = 6        /* the handle is poisoned by an earlier error */
+  LBM_ERR_STATE = 6,       /* the handle is poisoned by an earlier error */
+  LBM_ERR_BOUNDS = 7       /* only in a library built with -DLBM_BOUNDS_CHECK: a kernel computed
+                            * a population address or auxiliary-field index outside its buffer
+                            * (the access was redirected to the buffer's first element) */
 } lbm_status;
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q27 = 1 } lbm_lattice;
@@ -371,9 +374,10 @@ const char* lbm_version(void);
 lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, int64_t nsteps);
 
 /* Outcome of the last lbm_step_noalloc call on the current device, for the same
- * callers (the paper has no counterpart): LBM_ERR_TIMEOUT if one of its bounded
- * device-side waits gave up (those tiles were left unwritten), else
- * LBM_ERR_UNSTABLE if a non-finite or non-positive density appeared, else LBM_OK;
+ * callers (the paper has no counterpart): LBM_ERR_BOUNDS (bounds-checked builds
+ * only) if a kernel computed an index outside its buffer, else LBM_ERR_TIMEOUT if
+ * one of its bounded device-side waits gave up (those tiles were left unwritten),
+ * else LBM_ERR_UNSTABLE if a non-finite or non-positive density appeared, else LBM_OK;
  * LBM_ERR_CUDA if the flag word cannot be read.  Reads the flag word at the start
  * of the shared scratch array into a host variable (no allocation); call it after
  * the stream that ran the steps has completed, before the next call clears it. */

@@ -23,7 +23,12 @@ static thread_local std::string g_create_error = "no error";
 
 namespace {
 
+#ifdef LBM_BOUNDS_CHECK
+const char* kVersion =
+    "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP32/FP16-deviation, A-A streaming, sm_103a, bounds-checked";
+#else
 const char* kVersion = "liblbm: entropic MRT two-phase LBM, D2Q9/D3Q27, FP64/FP32/FP16-deviation, A-A streaming, sm_103a";
+#endif
 
 using lbm::EosCoeffs;
 using lbm::eos_coeffs;
@@ -188,8 +193,10 @@ lbm_status drain_marks(lbm_domain* h) {
   return LBM_OK;
 }
 
-// Status for the device error word: bit 0 instability, bit 1 a bounded wait gave up.
+// Status for the device error word: bit 0 instability, bit 1 a bounded wait gave up,
+// bit 2 an out-of-range index caught by a bounds-checked build.
 lbm_status flags_status(lbm_domain* h, unsigned int flags) {
+  if (flags & 4u) return fail(h, LBM_ERR_BOUNDS, "a kernel computed an index outside its buffer (bounds-checked build)");
   if (flags & 2u) return fail(h, LBM_ERR_TIMEOUT, "a bounded device-side wait for a TMA tile gave up");
   if (flags & 1u) return fail(h, LBM_ERR_UNSTABLE, "non-finite or non-positive density in the domain");
   return LBM_OK;

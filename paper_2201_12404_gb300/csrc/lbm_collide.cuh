@@ -522,7 +522,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
   const bool active = x < d.nx && y < d.ny && z < d.nz;
   const long long n = node_of(d, x, y, z);
   const bool fast = P == 0 || fast_links<D>(d, x, y, z);
-  const long long pc = pnode_of<D>(d, x, y, z);
+  const long long pc = active ? bc_pnode(d, pnode_of<D>(d, x, y, z)) : 0;
 
   // the node's force (Eq. Kforce_final), from pass 1b
   A Fa[3] = {0, 0, 0};
@@ -584,7 +584,7 @@ __device__ __forceinline__ bool collide_tile(const DevDomain& d, const TileMaps*
     for (int a = 0; a < D; ++a) {
       const A* qa = a_q + a * d.PN;
       const long long e = a == 0 ? 1 : (a == 1 ? sy : sz);
-      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[pc - e] - (R)qa[pc + e]) * (R)0.5;
+      Phi[a] = ((R)1 - (R)0.5 * om) * ((R)qa[bc_pnode(d, pc - e)] - (R)qa[bc_pnode(d, pc + e)]) * (R)0.5;
     }
   }
   if (kStaged) {
@@ -654,7 +654,7 @@ __device__ __forceinline__ void qflux_load_j(const DevDomain& d, int x0, int y0,
   for (int k = 0; k < TK; ++k) {
     const int y = y0 + (D == 3 ? (int)threadIdx.y : (int)threadIdx.y + TY * k), z = z0 + (D == 3 ? k : 0);
     const bool in = x < d.nx && y < d.ny && z < d.nz;
-    const long long pn = in ? pnode_of<D>(d, x, y, z) : 0;
+    const long long pn = in ? bc_pnode(d, pnode_of<D>(d, x, y, z)) : 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) jn[k][a] = in ? aux[(2 + D + a) * d.PN + pn] : (A)0;
   }
@@ -667,7 +667,7 @@ template <int D, typename R, typename A>
 __device__ __forceinline__ void qflux_store(const DevDomain& d, int x, int y, int z, int gx, bool gw_x, R rho,
                                             const A (&j)[3], const R (&F)[3]) {
   A* aux = (A*)d.aux;
-  const long long pn = pnode_of<D>(d, x, y, z);
+  const long long pn = bc_pnode(d, pnode_of<D>(d, x, y, z));
   const R inv = (R)1 / rho;
   A q[3];
 #pragma unroll
@@ -686,7 +686,7 @@ __device__ __forceinline__ void qflux_store(const DevDomain& d, int x, int y, in
     if (((m & 1) && gx < 0) || ((m & 2) && gy < 0) || ((m & 4) && gz < 0)) continue;
     const int cx = (m & 1) ? gx : x + 2, cy = (m & 2) ? gy : y + 2, cz = D == 3 ? ((m & 4) ? gz : z + 2) : 0;
     const bool flip = ((m & 1) && gw_x) || ((m & 2) && gw_y) || ((m & 4) && gw_z);
-    const long long g = (long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz);
+    const long long g = bc_pnode(d, (long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz));
 #pragma unroll
     for (int a = 0; a < D; ++a) aux[(2 + a) * d.PN + g] = flip ? -q[a] : q[a];
   }
@@ -759,7 +759,7 @@ __device__ __forceinline__ void qflux_nodes_zwalk(const DevDomain& d, int x0, in
       // the momenta of the node whose first plane this is, four planes before use
       const bool in = z0 + hz < d.nz;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) j[hz][a] = in ? aj[a * d.PN + pj + hz * plane] : (A)0;
+      for (int a = 0; a < 3; ++a) j[hz][a] = in ? aj[a * d.PN + bc_pnode(d, pj + hz * plane)] : (A)0;
 #pragma unroll
       for (int a = 0; a < 3; ++a) G[hz][a] = zero2;
     }

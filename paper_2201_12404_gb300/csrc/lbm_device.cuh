@@ -87,7 +87,8 @@ struct DevDomain {
   void* f;             // populations (storage type)
   void* aux;           // padded auxiliary fields (float64 in the FP64 path, float32 otherwise)
   float* gamma_out;    // per-node (gamma, omega) pairs of the last step, or nullptr
-  unsigned int* flags; // bit 0: non-finite or non-positive density seen
+  unsigned int* flags; // bit 0: non-finite or non-positive density seen; bit 1: a bounded
+                       // wait gave up; bit 2: an out-of-range index (bounds-checked builds)
   unsigned long long* guards; // nodes where f*_i <= 0 forced gamma = 2
   long long N, PN;     // interior and padded node counts
   int nx, ny, nz;      // nz = 1 in 2-D
@@ -208,6 +209,32 @@ __device__ __forceinline__ XBase xbase(const DevDomain& d, int x, long long n) {
   return r;
 }
 
+// Bounds-checked builds (-DLBM_BOUNDS_CHECK, the stand-in for a memory checker):
+// every computed population address and auxiliary-field index is checked against
+// its buffer; one outside it sets bit 2 of the error word (LBM_ERR_BOUNDS) and is
+// replaced by the buffer's first element, so that the access stays in bounds.
+// Regular builds compile the checks away.
+__device__ __forceinline__ long long bc_index(const DevDomain& d, long long i, long long n) {
+#ifdef LBM_BOUNDS_CHECK
+  if (i < 0 || i >= n) {
+    atomicOr(d.flags, 4u);
+    return 0;
+  }
+#endif
+  return i;
+}
+// A padded auxiliary node index (a (rho, psi) pair or one element of a plane).
+__device__ __forceinline__ long long bc_pnode(const DevDomain& d, long long pn) { return bc_index(d, pn, d.PN); }
+// A population slot address in d.f.
+template <int D, typename S>
+__device__ __forceinline__ S* bc_pop(const DevDomain& d, S* p) {
+#ifdef LBM_BOUNDS_CHECK
+  return (S*)d.f + bc_index(d, (long long)(p - (S*)d.f), (long long)Lattice<D>::Q * d.N);
+#else
+  return p;
+#endif
+}
+
 // Neighbour coordinate along one axis: periodic wrap, or wall = true when the
 // link crosses a bounce-back wall.
 __device__ __forceinline__ int step_axis(int x, int c, int n, int wlo, int whi, bool& wall) {
@@ -225,13 +252,13 @@ __device__ __forceinline__ S* src_ptr(const DevDomain& d, bool fast, const XBase
                                       int i) {
   constexpr int Q = Lattice<D>::Q;
   S* F = (S*)d.f;
-  if (P == 0) return (S*)(xb.p[1] + d.src_boff[0][i]);
-  if (fast) return (S*)(xb.p[cxi(i) + 1] + d.src_boff[1][i]);
+  if (P == 0) return bc_pop<D>(d, (S*)(xb.p[1] + d.src_boff[0][i]));
+  if (fast) return bc_pop<D>(d, (S*)(xb.p[cxi(i) + 1] + d.src_boff[1][i]));
   bool wall = false;
   const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
   const int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-  return F + (wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz));
+  return bc_pop<D>(d, F + (wall ? (long long)i * d.N + n : (long long)(Q - 1 - i) * d.N + node_of(d, sx, sy, sz)));
 }
 
 // Slot receiving the post-collision population i of node (x,y,z) at parity P:
@@ -242,13 +269,13 @@ __device__ __forceinline__ S* dst_ptr(const DevDomain& d, bool fast, const XBase
                                       int i) {
   constexpr int Q = Lattice<D>::Q;
   S* F = (S*)d.f;
-  if (P == 0) return (S*)(xb.p[1] + d.dst_boff[0][i]);
-  if (fast) return (S*)(xb.p[1 - cxi(i)] + d.dst_boff[1][i]);
+  if (P == 0) return bc_pop<D>(d, (S*)(xb.p[1] + d.dst_boff[0][i]));
+  if (fast) return bc_pop<D>(d, (S*)(xb.p[1 - cxi(i)] + d.dst_boff[1][i]));
   bool wall = false;
   const int tx = step_axis(x, cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int ty = step_axis(y, cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
   const int tz = D == 3 ? step_axis(z, czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-  return F + (wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz));
+  return bc_pop<D>(d, F + (wall ? (long long)(Q - 1 - i) * d.N + n : (long long)i * d.N + node_of(d, tx, ty, tz)));
 }
 
 // Node that wrote the slot population i of node (x,y,z) is read from: the
@@ -256,12 +283,12 @@ __device__ __forceinline__ S* dst_ptr(const DevDomain& d, bool fast, const XBase
 template <int D>
 __device__ __forceinline__ long long upstream_node(const DevDomain& d, bool fast, const XBase& xb, int x, int y, int z,
                                                    long long n, int i) {
-  if (fast) return xb.b[cxi(i) + 1] + d.up_off[i];
+  if (fast) return bc_index(d, xb.b[cxi(i) + 1] + d.up_off[i], d.N);
   bool wall = false;
   const int sx = step_axis(x, -cxi(i), d.nx, d.wall_lo[0], d.wall_hi[0], wall);
   const int sy = step_axis(y, -cyi(i), d.ny, d.wall_lo[1], d.wall_hi[1], wall);
   const int sz = D == 3 ? step_axis(z, -czi(i), d.nz, d.wall_lo[2], d.wall_hi[2], wall) : 0;
-  return wall ? n : node_of(d, sx, sy, sz);
+  return bc_index(d, wall ? n : node_of(d, sx, sy, sz), d.N);
 }
 
 template <int D, int P, typename S, typename R>

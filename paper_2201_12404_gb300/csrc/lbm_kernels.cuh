@@ -51,7 +51,7 @@ __device__ __forceinline__ void moments_eos_node(const DevDomain& d, int x, int 
 
   A* aux = (A*)d.aux;
   Two<A>* a2 = (Two<A>*)d.aux;
-  const long long pn = pnode_of<D>(d, x, y, z);
+  const long long pn = bc_pnode(d, pnode_of<D>(d, x, y, z));
   const Two<A> pair = two<A>((A)rho, (A)psi_of<R>(d, rho));
   a2[pn] = pair;
 #pragma unroll
@@ -65,7 +65,7 @@ __device__ __forceinline__ void moments_eos_node(const DevDomain& d, int x, int 
   for (int m = 1; m < (1 << D); ++m) {
     if (((m & 1) && gx < 0) || ((m & 2) && gy < 0) || ((m & 4) && gz < 0)) continue;
     const int cx = (m & 1) ? gx : x + 2, cy = (m & 2) ? gy : y + 2, cz = D == 3 ? ((m & 4) ? gz : z + 2) : 0;
-    a2[(long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz)] = pair;
+    a2[bc_pnode(d, (long long)cx + (long long)d.px * ((long long)cy + (long long)d.py * cz))] = pair;
   }
 }
 

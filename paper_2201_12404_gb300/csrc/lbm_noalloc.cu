@@ -103,6 +103,7 @@ extern "C" lbm_status lbm_noalloc_status(void) {
   unsigned int flags = 0;
   // a pageable host word: the copy allocates nothing
   if (cudaMemcpy(&flags, scratch, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ERR_CUDA;
+  if (flags & 4u) return LBM_ERR_BOUNDS;
   if (flags & 2u) return LBM_ERR_TIMEOUT;
   if (flags & 1u) return LBM_ERR_UNSTABLE;
   return LBM_OK;

@@ -18,9 +18,12 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblbm.so")
+# LBM_LIBRARY may name another build of the library (the bounds-checked one of
+# build.build_bounds_checked); the default is the in-tree liblbm.so.
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "liblbm.so")
 
-LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
+(LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE,
+ LBM_ERR_BOUNDS) = range(8)
 LBM_D2Q9, LBM_D3Q27 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
@@ -31,7 +34,7 @@ DEV_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 DEV_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
-                4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+                4: "LBM_ERR_UNSTABLE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE", 7: "LBM_ERR_BOUNDS"}
 
 
 class lbm_params(ctypes.Structure):
