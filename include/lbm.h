@@ -144,9 +144,11 @@ lbm_status lbm_create_domain(const lbm_params* p, lbm_handle* out);
 lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, const double* uy,
                            const double* uz);
 
-/* Advance nsteps >= 0 time steps (asynchronous).  An instability detected by
- * an earlier call surfaces here or in any later synchronising call as
- * LBM_ERR_UNSTABLE. */
+/* Advance nsteps >= 0 time steps of Eq. (LBGK) (asynchronous).  A step is three
+ * kernels: moments and the Peng-Robinson pseudo-potential (Sec. 2.3); the force
+ * of Eq. (Kforce_final) and the flux q of Eq. (correction); the collision of
+ * Sec. 2.4 with the A-A stream.  An instability detected by an earlier call
+ * surfaces here or in any later synchronising call as LBM_ERR_UNSTABLE. */
 lbm_status lbm_step(lbm_handle h, int64_t nsteps);
 
 /* Wait for the domain's stream; report LBM_ERR_UNSTABLE if a non-finite or
@@ -265,8 +267,9 @@ lbm_status lbm_psi_sign_changes(const lbm_params* p, double changes[3], int* n, 
 /* Kernel timing on the domain's stream with CUDA events.  When enabled, every
  * launch made by lbm_step is bracketed by events; lbm_kernel_times then
  * synchronises and returns, per kernel kind, the summed milliseconds and the
- * launch count: ms[0]/count[0] moments+EOS kernel, ms[1]/count[1]
- * force+collide+stream kernel.  Enabling resets the sums. */
+ * launch count: ms[0]/count[0] the moments+EOS kernel and the force+q kernel that
+ * follows it (timed together; two launches a step), ms[1]/count[1] the
+ * collide+stream kernel.  Enabling resets the sums. */
 lbm_status lbm_set_timing(lbm_handle h, int enable);
 lbm_status lbm_kernel_times(lbm_handle h, double ms[2], int64_t count[2]);
 
@@ -282,8 +285,9 @@ const char* lbm_last_error(lbm_handle h);
  * A batch holds D2Q9 domains of one precision and any sizes and parameters.
  * lbm_batch_step advances all of them by nsteps time steps with a single
  * cooperative (all blocks resident) kernel launch: the blocks walk a work list of
- * (domain, tile) items for pass 1, meet at a grid barrier, walk the pass-2 items,
- * and repeat per step.  Every grid-barrier wait is bounded; a wait that gives up
+ * (domain, tile) items for pass 1 (moments, EOS), meet at a grid barrier, walk it
+ * for pass 1b (force, q), meet again, walk it for pass 2 (collide, stream), and
+ * repeat per step.  Every grid-barrier wait is bounded; a wait that gives up
  * stops the kernel and surfaces as LBM_ERR_TIMEOUT.  The launch is captured in a
  * CUDA graph per distinct nsteps (replayed afterwards) when the driver accepts
  * capturing a cooperative launch, and launched directly otherwise.  Work runs on

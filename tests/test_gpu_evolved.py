@@ -86,7 +86,7 @@ def test_static_drop_128_evolved_states_match_oracle(precision):
 @pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_FP32], ids=["fp64", "fp32"])
 def test_drop_on_film_64cubed_evolved_states_match_oracle(precision):
     """The D3Q27 drop impact (T/Tc 0.59, density ratio ~1000, z walls) on a 64^3 box
-    at steps 0 and 50 (in float32 the single-pass step)."""
+    at steps 0 and 50."""
     wl = WL.DROP_IMPACT_3D
     errs = evolve_and_compare(wl, precision, [0, 50], (64, 64, 64))
     check(errs, precision)
