@@ -55,7 +55,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int* er
 template <int BX, int BY, typename S, typename R, typename A>
 __global__ void __launch_bounds__(BX * BY, sizeof(R) == 4 ? LBM_BATCH_MINBLOCKS_F32 : 1) batch_persistent_kernel(BatchArgs a) {
   __shared__ __align__(128) Two<A> s_aux[Halo<2, BX, BY, 1>::HN];
-  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
   R* s_h = (R*)smem_dyn;
   for (int s = 0; s < a.nsteps; ++s) {
     // pass 1 over the interior tiles (each node also writes its ghost images)
