@@ -77,9 +77,10 @@ def check(errs, precision):
 
 @pytest.mark.parametrize("precision", [lbm.LBM_FP64, lbm.LBM_FP32], ids=["fp64", "fp32"])
 def test_static_drop_128_evolved_states_match_oracle(precision):
-    """The D2Q9 static drop (128x128 periodic, T/Tc 0.8, R = 25) at steps 10, 100 and 1000."""
+    """The D2Q9 static drop (128x128 periodic, T/Tc 0.8, R = 25) at steps 0, 1, 10, 100
+    and 1000."""
     wl = WL.STATIC_DROP_2D
-    errs = evolve_and_compare(wl, precision, [10, 100, 1000], (1, 128, 128))
+    errs = evolve_and_compare(wl, precision, [0, 1, 10, 100, 1000], (1, 128, 128))
     check(errs, precision)
 
 
