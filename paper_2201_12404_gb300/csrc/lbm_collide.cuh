@@ -24,12 +24,13 @@
 
 #include "lbm_device.cuh"
 
-// Minimum resident 256-thread blocks per SM requested from the register
-// allocator in the float32 path: three for D3Q27 (80 registers), five for D2Q9,
-// whose nine populations a node fit in 48 registers (2048x1024 impact: pass 2
-// 57.6 us per launch at three blocks, 49.5 at four, 46.9 at five).
+// Minimum resident blocks per SM requested from the register allocator in the
+// float32 path: twelve 64-thread blocks for D3Q27 (80 registers; 64 registers for
+// sixteen spill and run slower), five 256-thread blocks for D2Q9, whose nine
+// populations a node fit in 48 registers (2048x1024 impact: pass 2 57.6 us per
+// launch at three blocks, 49.5 at four, 46.9 at five).
 #ifndef LBM_K2_MINBLOCKS_F32
-#define LBM_K2_MINBLOCKS_F32 3
+#define LBM_K2_MINBLOCKS_F32 12
 #endif
 #ifndef LBM_K2_MINBLOCKS_F32_2D
 #define LBM_K2_MINBLOCKS_F32_2D 5

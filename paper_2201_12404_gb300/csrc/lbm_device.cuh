@@ -42,7 +42,17 @@ template <int D> __host__ __device__ constexpr double wq(int i) {
 // stages the q planes of a tile of this shape plus a 1-node halo (2 along x).
 template <int D> struct Blocks;
 template <> struct Blocks<2> { static constexpr int bx = 64, by = 4, bz = 1; };
-template <> struct Blocks<3> { static constexpr int bx = 32, by = 4, bz = 2; };
+// D3Q27: 64-thread blocks of 32x2x1 nodes.  With pass 2's 80 registers, twelve of
+// them fill an SM (24 warps, as three 256-thread blocks would) but retire and
+// refill in finer steps: on the 512x512x256 impact pass 2 takes 3.03 ms per launch
+// against 3.18 with 32x4x2, 3.06 with 32x2x2 and 3.08 with 32x4x1 blocks.
+#ifndef LBM_BLOCK3_Y
+#define LBM_BLOCK3_Y 2
+#endif
+#ifndef LBM_BLOCK3_Z
+#define LBM_BLOCK3_Z 1
+#endif
+template <> struct Blocks<3> { static constexpr int bx = 32, by = LBM_BLOCK3_Y, bz = LBM_BLOCK3_Z; };
 
 // Physical parameters in the arithmetic type of a path (filled on the host, so
 // that kernels never convert float64 parameters on the slow float64 pipe).
