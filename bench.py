@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+E2E_REPEATS = 3  # end-to-end passes; the line reports the median
 
 
 def measured_peaks():
@@ -359,16 +360,21 @@ def run_ours(args):
                             h_u[2].data_ptr() if wl.D == 3 else None)
     dom.lbm_read_macroscopic_ptr(o_rho.data_ptr(), o_u[0].data_ptr(), o_u[1].data_ptr(),
                                  o_u[2].data_ptr() if wl.D == 3 else None)
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    dom.lbm_init_fields_ptr(h_rho.data_ptr(), h_u[0].data_ptr(), h_u[1].data_ptr(),
-                            h_u[2].data_ptr() if wl.D == 3 else None)
-    dom.lbm_step(args.steps)
-    dom.lbm_read_macroscopic_ptr(o_rho.data_ptr(), o_u[0].data_ptr(), o_u[1].data_ptr(),
-                                 o_u[2].data_ptr() if wl.D == 3 else None)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    assert np.isfinite(o_rho.numpy()).all(), "non-finite density after the e2e run"
+    # three timed passes, the median reported (a single pass right after the timed
+    # region above scattered by up to 10% from run to run)
+    e2e_runs = []
+    for _ in range(E2E_REPEATS):
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dom.lbm_init_fields_ptr(h_rho.data_ptr(), h_u[0].data_ptr(), h_u[1].data_ptr(),
+                                h_u[2].data_ptr() if wl.D == 3 else None)
+        dom.lbm_step(args.steps)
+        dom.lbm_read_macroscopic_ptr(o_rho.data_ptr(), o_u[0].data_ptr(), o_u[1].data_ptr(),
+                                     o_u[2].data_ptr() if wl.D == 3 else None)
+        e2e_runs.append(max_over_ranks(time.perf_counter() - t0, world))
+        assert np.isfinite(o_rho.numpy()).all(), "non-finite density after the e2e run"
+    e2e_s = sorted(e2e_runs)[len(e2e_runs) // 2]
     e2e_mlups = wl.N * args.steps * world / e2e_s / 1e6
     dom.close()
 
@@ -420,7 +426,8 @@ def run_ours(args):
         "e2e": {"value": e2e_mlups, "unit": "MLUPS",
                 "h2d_bytes_per_step": (1 + wl.D) * wl.N * 8 / args.steps,
                 "d2h_bytes_per_step": (1 + wl.D) * wl.N * 8 / args.steps,
-                "what": "lbm_init_fields from pinned host arrays + K steps + lbm_read_macroscopic to pinned host"},
+                "what": "lbm_init_fields from pinned host arrays + K steps + lbm_read_macroscopic to pinned host; "
+                        f"median of {E2E_REPEATS} passes", "passes_s": e2e_runs},
         "gpu_launches": launches,
         "clocks": clocks,
     }
