@@ -133,13 +133,18 @@ struct TileMaps {
 // nodes along z (tile TX x TY x TK), in 2-D along y (tile TX x TY*TK).  Taller
 // tiles than pass 2's keep the staged halo small against the tile: pass 1b does
 // little arithmetic per node, so the halo traffic would dominate.  kPairBytes is
-// the size of one staged (rho, psi) pair.  In float32 3-D, TK = 8: a 41 KB tile,
-// three blocks per SM (see LBM_QFLUX_MINBLOCKS).
+// the size of one staged (rho, psi) pair.  In float32 3-D, 32x8 threads with TK = 8:
+// a 41 KB tile, three blocks per SM (see LBM_QFLUX_MINBLOCKS).  Passes 1 + 1b on the
+// 512x512x256 impact: 2.06 ms, against 2.08 with 32x4 threads (six blocks per SM),
+// 2.16 with 32x2 (ten) and 2.19 with 32x4 threads and TK = 16.
 #ifndef LBM_QTILE_TK3_F32
 #define LBM_QTILE_TK3_F32 8
 #endif
+#ifndef LBM_QTILE_TY3
+#define LBM_QTILE_TY3 8
+#endif
 template <int D, int kPairBytes> struct QTile {
-  static constexpr int TX = D == 3 ? 32 : 64, TY = D == 3 ? 8 : 4;
+  static constexpr int TX = D == 3 ? 32 : 64, TY = D == 3 ? LBM_QTILE_TY3 : 4;
   static constexpr int TK = D == 3 ? (kPairBytes == 8 ? LBM_QTILE_TK3_F32 : 4) : 4;
   static constexpr int EX = TX, EY = D == 3 ? TY : TY * TK, EZ = D == 3 ? TK : 1;  // tile extents
   static constexpr int HX = EX + 4, HY = EY + 4, HZ = D == 3 ? EZ + 4 : 1;         // with the halo
