@@ -25,12 +25,14 @@
 #include "lbm_device.cuh"
 
 // Minimum resident blocks per SM requested from the register allocator in the
-// float32 path: twelve 64-thread blocks for D3Q27 (80 registers; 64 registers for
-// sixteen spill and run slower), five 256-thread blocks for D2Q9, whose nine
-// populations a node fit in 48 registers (2048x1024 impact: pass 2 57.6 us per
-// launch at three blocks, 49.5 at four, 46.9 at five).
+// float32 path.  D3Q27: ten 64-thread blocks, i.e. up to 96 registers and no
+// spills, 20 warps per SM (512x512x256 impact, pass 2 per launch: 2.72 ms, against
+// 3.03 at twelve blocks and 80 registers with ~90 bytes spilled, 2.99 at eight and
+// ~112 registers).  D2Q9: five 256-thread blocks, whose nine populations a node
+// fit in 48 registers (2048x1024 impact: pass 2 57.6 us per launch at three
+// blocks, 49.5 at four, 46.9 at five).
 #ifndef LBM_K2_MINBLOCKS_F32
-#define LBM_K2_MINBLOCKS_F32 12
+#define LBM_K2_MINBLOCKS_F32 10
 #endif
 #ifndef LBM_K2_MINBLOCKS_F32_2D
 #define LBM_K2_MINBLOCKS_F32_2D 5

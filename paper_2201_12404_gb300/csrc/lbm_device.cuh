@@ -42,10 +42,11 @@ template <int D> __host__ __device__ constexpr double wq(int i) {
 // stages the q planes of a tile of this shape plus a 1-node halo (2 along x).
 template <int D> struct Blocks;
 template <> struct Blocks<2> { static constexpr int bx = 64, by = 4, bz = 1; };
-// D3Q27: 64-thread blocks of 32x2x1 nodes.  With pass 2's 80 registers, twelve of
-// them fill an SM (24 warps, as three 256-thread blocks would) but retire and
-// refill in finer steps: on the 512x512x256 impact pass 2 takes 3.03 ms per launch
-// against 3.18 with 32x4x2, 3.06 with 32x2x2 and 3.08 with 32x4x1 blocks.
+// D3Q27: 64-thread blocks of 32x2x1 nodes, which retire and refill an SM in finer
+// steps than 256-thread blocks: at 80 registers (24 warps per SM) pass 2 took
+// 3.03 ms per launch on the 512x512x256 impact against 3.18 with 32x4x2, 3.06 with
+// 32x2x2 and 3.08 with 32x4x1 blocks; at 96 registers (LBM_K2_MINBLOCKS_F32) 2.72
+// against 2.75 with 32x2x2 and 2.78 with 32x1x1 blocks.
 #ifndef LBM_BLOCK3_Y
 #define LBM_BLOCK3_Y 2
 #endif
