@@ -247,6 +247,48 @@ lbm_status launch_k(lbm_domain* h, int kind) {
   return LBM_OK;
 }
 
+// Launch the graph of two steps from the current parity, capturing it first if
+// there is none for this parity and gamma record.  *replayed is false (and nothing
+// was enqueued) when capture is not possible on this stream; the domain then keeps
+// to plain launches.
+lbm_status launch_pair_graph(lbm_domain* h, bool* replayed) {
+  *replayed = false;
+  const int p = h->parity;
+  if (!h->step_graph[p] || h->step_graph_gamma[p] != h->dev.gamma_out) {
+    if (h->step_graph[p]) {
+      cudaGraphExecDestroy(h->step_graph[p]);
+      h->step_graph[p] = nullptr;
+    }
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs_ok = false;
+      return LBM_OK;
+    }
+    for (int k = 0; k < 2; ++k) {
+      const int par = p ^ k;
+      h->ops->moments_eos(h->dev, par, h->stream);
+      h->ops->qflux(h->dev, h->maps, h->stream);
+      h->ops->collide_stream(h->dev, h->maps, par, h->stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || !exec) {
+      cudaGetLastError();  // the failed capture left nothing on the stream
+      h->graphs_ok = false;
+      return LBM_OK;
+    }
+    h->step_graph[p] = exec;
+    h->step_graph_gamma[p] = (float*)h->dev.gamma_out;
+  }
+  LBM_CUDA(h, cudaGraphLaunch(h->step_graph[p], h->stream));
+  h->launches += 6;
+  *replayed = true;
+  return LBM_OK;
+}
+
 // Run pass 1 for the current state (refreshes the auxiliary fields).
 lbm_status refresh_aux(lbm_domain* h) {
   h->ops->moments_eos(h->dev, h->parity, h->stream);
@@ -474,6 +516,8 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& m : h->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  for (auto& g : h->step_graph)
+    if (g) cudaGraphExecDestroy(g);
   keep_free(h->p, h->dev.f);
   keep_free(h->p, h->dev.aux);
   keep_free(h->p, h->dev.rho_w[0]);
@@ -554,11 +598,22 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
   if (h->record_gamma && nsteps > 0) h->gamma_recorded = true;
   DevDomain saved = h->dev;
   if (!h->record_gamma) h->dev.gamma_out = nullptr;
-  for (int64_t s = 0; s < nsteps; ++s) {
+  for (int64_t s = 0; s < nsteps;) {
+    if (!h->timing && h->graphs_ok && h->plain_steps >= 2 && nsteps - s >= 2) {
+      bool replayed = false;
+      if ((st = launch_pair_graph(h, &replayed)) != LBM_OK) break;
+      if (replayed) {
+        h->steps += 2;  // two steps: the parity is back where it was
+        s += 2;
+        continue;
+      }
+    }
     if ((st = launch_k(h, 0)) != LBM_OK) break;
     if ((st = launch_k(h, 1)) != LBM_OK) break;
     h->parity ^= 1;
     h->steps += 1;
+    h->plain_steps += 1;
+    s += 1;
   }
   h->dev.gamma_out = saved.gamma_out;
   if (st != LBM_OK) return st;

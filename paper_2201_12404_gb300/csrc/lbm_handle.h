@@ -35,6 +35,15 @@ struct lbm_domain {
   int64_t cnt[2] = {0, 0};
   bool record_gamma = false;
   bool gamma_recorded = false;  // a step has run with recording on since the buffer was made
+  // CUDA graphs of two consecutive steps starting at parity p (the three kernels of
+  // parity p, then of 1 - p), replayed by lbm_step when timing is off.  A graph holds
+  // the kernel arguments of its capture, so it is keyed by the only device pointer
+  // that changes after creation, the gamma record (nullptr while not recording).
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  float* step_graph_gamma[2] = {nullptr, nullptr};
+  bool graphs_ok = true;   // cleared if capture or instantiation fails: plain launches then
+  int64_t plain_steps = 0; // steps launched one kernel at a time (the launchers set their
+                           // kernel attributes on first use, outside any capture)
 };
 
 // Mark the domain's error word as copied to the host after work enqueued on `stream`

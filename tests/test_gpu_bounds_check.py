@@ -4,7 +4,7 @@ With -DLBM_BOUNDS_CHECK every population address and auxiliary-field index a
 kernel computes is checked against its buffer; one outside it is redirected to
 the buffer's first element and reported as LBM_ERR_BOUNDS, which the binding
 raises.  Running the oracle-parity suites (every lattice, precision and wall
-layout, the batch kernel, the allocation-free step, evolved states) on that build
+layout, the batch kernel, graph replay, the allocation-free step, evolved states) on that build
 in a child process shows that no step of theirs computes an index outside its
 buffer; the suites' own oracle checks hold there too (the checks change no
 arithmetic).
@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_fp16dev.py", "tests/test_gpu_batch.py",
-          "tests/test_gpu_evolved.py", "tests/test_zz_no_alloc.py"]
+          "tests/test_gpu_evolved.py", "tests/test_gpu_graphs.py", "tests/test_zz_no_alloc.py"]
 
 
 def test_parity_suites_stay_in_bounds_on_the_checked_build():
