@@ -147,8 +147,11 @@ lbm_status lbm_init_fields(lbm_handle h, const double* rho, const double* ux, co
 /* Advance nsteps >= 0 time steps of Eq. (LBGK) (asynchronous).  A step is three
  * kernels: moments and the Peng-Robinson pseudo-potential (Sec. 2.3); the force
  * of Eq. (Kforce_final) and the flux q of Eq. (correction); the collision of
- * Sec. 2.4 with the A-A stream.  An instability detected by an earlier call
- * surfaces here or in any later synchronising call as LBM_ERR_UNSTABLE. */
+ * Sec. 2.4 with the A-A stream.  With timing off, once the domain has run two
+ * steps, pairs of steps are replayed as a captured CUDA graph of those kernels
+ * (same kernels and arguments, bit-identical results; recaptured when the gamma
+ * record is switched on).  An instability detected by an earlier call surfaces
+ * here or in any later synchronising call as LBM_ERR_UNSTABLE. */
 lbm_status lbm_step(lbm_handle h, int64_t nsteps);
 
 /* Wait for the domain's stream; report LBM_ERR_UNSTABLE if a non-finite or
@@ -269,7 +272,8 @@ lbm_status lbm_psi_sign_changes(const lbm_params* p, double changes[3], int* n, 
  * synchronises and returns, per kernel kind, the summed milliseconds and the
  * launch count: ms[0]/count[0] the moments+EOS kernel and the force+q kernel that
  * follows it (timed together; two launches a step), ms[1]/count[1] the
- * collide+stream kernel.  Enabling resets the sums. */
+ * collide+stream kernel.  Enabling resets the sums; while enabled, lbm_step
+ * launches kernel by kernel (no graph replay). */
 lbm_status lbm_set_timing(lbm_handle h, int enable);
 lbm_status lbm_kernel_times(lbm_handle h, double ms[2], int64_t count[2]);
 
