@@ -159,7 +159,10 @@ def oracle_crop_state(wl, crop=CPU_CROP):
 
 
 def crop_of(wl):
-    return CPU_CROP if wl.D == 3 else CPU_CROP_2D
+    """The oracle's crop of a workload: CPU_CROP (3-D) or CPU_CROP_2D, clipped to the
+    domain (the 128x128 static drop is timed whole)."""
+    crop = CPU_CROP if wl.D == 3 else CPU_CROP_2D
+    return tuple(min(c, n) for c, n in zip(crop, (wl.nz, wl.ny, wl.nx)))
 
 
 def lattice_of(wl):
@@ -452,9 +455,9 @@ def main():
                     help="fraction of each served job's 1,000-10,000 steps")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16dev"], default="fp32",
                     help="population storage/arithmetic of the timed path (fp32 is the headline)")
-    ap.add_argument("--workload", default="drop3d", choices=["drop3d", "drop3d-small", "drop2d"],
+    ap.add_argument("--workload", default="drop3d", choices=["drop3d", "drop3d-small", "drop2d", "static2d"],
                     help="drop3d (default, D3Q27 512x512x256), drop3d-small (256x256x128, the profiling "
-                    "case) or drop2d (D2Q9 2048x1024)")
+                    "case), drop2d (D2Q9 2048x1024) or static2d (D2Q9 128x128 static drop, T/Tc = 0.8)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -82,6 +82,18 @@ def test_pass1_bytes_count_the_padded_auxiliary_fields():
     assert bench.algorithmic_bytes_k1(wl, 4, 4) == wl.N * 27 * 4 + pn * 7 * 4 + wl.N * 9 * 4
 
 
+def test_oracle_crop_is_clipped_to_the_domain():
+    """The oracle's sample is a crop of the benchmark domain, never larger than it:
+    the 128x128 static drop is timed whole, the impacts on their fixed crops."""
+    from paper_2201_12404_gb300 import workloads as WL
+    assert bench.crop_of(WL.by_name("static2d")) == (1, 128, 128)
+    assert bench.crop_of(WL.by_name("drop2d")) == bench.CPU_CROP_2D
+    assert bench.crop_of(WL.by_name("drop3d")) == bench.CPU_CROP
+    for name in ("static2d", "drop2d", "drop3d", "drop3d-small"):
+        wl = WL.by_name(name)
+        assert all(c <= n for c, n in zip(bench.crop_of(wl), (wl.nz, wl.ny, wl.nx)))
+
+
 
 def _dict_keys(node):
     import ast
