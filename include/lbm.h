@@ -391,6 +391,32 @@ lbm_status lbm_step_noalloc(const lbm_params* p, void* populations, int64_t nste
  * the stream that ran the steps has completed, before the next call clears it. */
 lbm_status lbm_noalloc_status(void);
 
+/* Host buffers for the calls that take host arrays (lbm_init_fields,
+ * lbm_read_macroscopic, lbm_read/write_populations and their windows).  The
+ * paper has no counterpart: these exist for the host-to-device path on Grace
+ * hosts, where a pageable or small-page pinned buffer that the GPU has not
+ * touched for a while copies several times slower than the NVLink-C2C link
+ * (the copy engines' address translation, not the bandwidth, sets the pace).
+ *
+ * lbm_host_alloc maps at least `bytes` bytes of zero-filled host memory at a
+ * transparent-huge-page boundary, rounded up to whole huge pages, asks the
+ * kernel for huge pages (advice: small pages where it has none) and registers
+ * the memory with the CUDA runtime (page-locked), so that copies from and to it
+ * run as direct transfers.  Where transparent huge pages are off, the buffer is
+ * page-locked memory with the system page size.  *out receives the start
+ * (aligned to the huge page, or page, size); the caller owns the buffer until
+ * lbm_host_free.  Returns LBM_ERR_INVALID_ARG for bytes == 0 or out == NULL,
+ * LBM_ERR_OOM if the mapping fails, LBM_ERR_CUDA if the registration fails (no
+ * CUDA device, for one); *out is NULL on any error.  Not synchronising; costs
+ * one pass of zero-filling over the memory.
+ *
+ * lbm_host_free unregisters and unmaps a buffer that lbm_host_alloc returned.
+ * NULL-safe; LBM_ERR_INVALID_ARG for any other pointer (nothing is released),
+ * LBM_ERR_CUDA if the unregistration fails (the memory is unmapped anyway).
+ * Thread-safe.  No copy or kernel may still be using the buffer. */
+lbm_status lbm_host_alloc(size_t bytes, void** out);
+lbm_status lbm_host_free(void* p);
+
 #ifdef __cplusplus
 }
 #endif

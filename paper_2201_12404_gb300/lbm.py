@@ -110,6 +110,8 @@ def load():
                 "lbm_version": (ctypes.c_char_p, []),
                 "lbm_step_noalloc": (st, [P, ctypes.c_void_p, ctypes.c_int64]),
                 "lbm_noalloc_status": (st, []),
+                "lbm_host_alloc": (st, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+                "lbm_host_free": (st, [ctypes.c_void_p]),
                 "lbm_batch_create": (st, [ctypes.POINTER(H), ctypes.c_int32, ctypes.POINTER(H)]),
                 "lbm_batch_step": (st, [H, ctypes.c_int64]),
                 "lbm_batch_synchronize": (st, [H]),
@@ -208,6 +210,41 @@ def lbm_step_noalloc(p: lbm_params, populations_ptr: int, nsteps: int) -> None:
 def lbm_noalloc_status() -> int:
     """Status of the last lbm_step_noalloc on the current device (after its stream completed)."""
     return int(load().lbm_noalloc_status())
+
+
+class HostBuffer:
+    """Page-locked host memory from lbm_host_alloc (huge-page backed where the kernel
+    allows), for the calls that take host arrays.  `array(dtype, count, offset)`
+    gives a numpy view; the views are valid until close()."""
+
+    def __init__(self, nbytes: int):
+        ptr = ctypes.c_void_p()
+        st = load().lbm_host_alloc(int(nbytes), ctypes.byref(ptr))
+        if st != LBM_OK:
+            raise LBMError(st, f"lbm_host_alloc of {int(nbytes)} bytes failed")
+        self.ptr, self.nbytes = int(ptr.value), int(nbytes)
+
+    def array(self, dtype, count: int, offset: int = 0):
+        import numpy as np
+        dt = np.dtype(dtype)
+        if offset < 0 or offset % dt.itemsize or offset + count * dt.itemsize > self.nbytes or not self.ptr:
+            raise ValueError("view outside the host buffer")
+        raw = (ctypes.c_char * (count * dt.itemsize)).from_address(self.ptr + offset)
+        return np.frombuffer(raw, dtype=dt, count=count)
+
+    def close(self):
+        if self.ptr:
+            st = load().lbm_host_free(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+            if st != LBM_OK:
+                raise LBMError(st, "lbm_host_free failed")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
 
 class lbm_drop_on_film(ctypes.Structure):

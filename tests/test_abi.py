@@ -146,3 +146,18 @@ def test_psi_sign_changes_match_oracle_sign(L, Tr, a):
         below, above = t * (1 - 1e-12), t * (1 + 1e-12)
         assert O.psi(op, below)[1] == lib_sign(below) and O.psi(op, above)[1] == lib_sign(above)
         assert lib_sign(below) == -lib_sign(above)
+
+
+def test_host_buffer_arguments_checked_before_any_cuda_call(L):
+    """lbm_host_alloc/lbm_host_free refuse what they cannot serve before they map or
+    register anything (the buffers themselves are tested on the GPU)."""
+    p = ctypes.c_void_p(1234)
+    assert L.lbm_host_alloc(0, ctypes.byref(p)) == lbm.LBM_ERR_INVALID_ARG and p.value is None
+    assert L.lbm_host_alloc(64, None) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_host_alloc(ctypes.c_size_t(-1).value, ctypes.byref(p)) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_host_free(None) == lbm.LBM_OK
+    assert L.lbm_host_free(ctypes.c_void_p(4096)) == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        hb = lbm.HostBuffer.__new__(lbm.HostBuffer)
+        hb.ptr, hb.nbytes = 0, 0
+        hb.array("f8", 1)
