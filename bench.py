@@ -139,7 +139,8 @@ def barrier(world):
 # ---------------------------------------------------------------------------
 CPU_CROP = (48, 64, 64)   # nz, ny, nx: 196,608 nodes
 CPU_CROP_2D = (1, 384, 512)
-CPU_STEPS = 12
+CPU_SAMPLE_S = 10.0   # seconds of oracle work in the bench line's cpu_baseline
+CPU_MAX_STEPS = 2000
 
 
 def oracle_crop_state(wl, crop=CPU_CROP):
@@ -170,13 +171,19 @@ def lattice_of(wl):
     return "D3Q27" if wl.D == 3 else "D2Q9"
 
 
-def oracle_sample(wl, steps=CPU_STEPS, crop=None):
+def oracle_sample(wl, target_s=CPU_SAMPLE_S, crop=None):
+    """The oracle on a crop of the workload for about target_s seconds: one step sets
+    the step count of the rest (at most CPU_MAX_STEPS), and every step is timed."""
     import oracle as O
     crop = crop or crop_of(wl)
     p, f = oracle_crop_state(wl, crop)
     nz, ny, nx = crop
     t0 = time.perf_counter()
-    O.run(p, f, steps)
+    f, _g = O.run(p, f, 1)
+    first = time.perf_counter() - t0
+    steps = 1 + max(0, min(CPU_MAX_STEPS, int((target_s - first) / max(first, 1e-6))))
+    if steps > 1:
+        O.run(p, f, steps - 1)
     dt = time.perf_counter() - t0
     lups = nx * ny * nz * steps
     return {"value": lups / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
