@@ -855,8 +855,11 @@ __device__ __forceinline__ void qflux_tile_staged(const DevDomain& d, int x0, in
 // Resident blocks per SM asked of the register allocator for pass 1b in float32:
 // three (80 registers, 8 bytes spilled in the 3-D walk of TK = 8; float64 takes
 // what it needs, 84).  On the 512x512x256
-// impact, passes 1 + 1b take 2.10 ms so, against 2.34 ms with TK = 4 at 76
-// registers, 2.18 ms with TK = 4 at 64 and 2.21 ms with TK = 8 at 64 (spills).
+// impact, passes 1 + 1b take 2.06-2.10 ms so, against 2.34 ms with TK = 4 at 76
+// registers, 2.18 ms with TK = 4 at 64 and 2.21 ms with TK = 8 at 64 (spills); a
+// deeper walk, fewer halo planes per node, was slower too: TK = 16 at 114 registers
+// (two 256-thread or four 128-thread blocks per SM, no spills) 2.14 and 2.20 ms,
+// TK = 16 or 12 at 80 registers (three blocks, ~20 bytes spilled) 2.19 and 2.16 ms.
 #ifndef LBM_QFLUX_MINBLOCKS
 #define LBM_QFLUX_MINBLOCKS 3
 #endif
