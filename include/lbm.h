@@ -398,13 +398,14 @@ lbm_status lbm_noalloc_status(void);
  * touched for a while copies several times slower than the NVLink-C2C link
  * (the copy engines' address translation, not the bandwidth, sets the pace).
  *
- * lbm_host_alloc maps at least `bytes` bytes of zero-filled host memory at a
- * transparent-huge-page boundary, rounded up to whole huge pages, asks the
- * kernel for huge pages (advice: small pages where it has none) and registers
- * the memory with the CUDA runtime (page-locked), so that copies from and to it
- * run as direct transfers.  Where transparent huge pages are off, the buffer is
- * page-locked memory with the system page size.  *out receives the start
- * (aligned to the huge page, or page, size); the caller owns the buffer until
+ * lbm_host_alloc maps at least `bytes` bytes of zero-filled host memory and
+ * registers it with the CUDA runtime (page-locked), so that copies from and to it
+ * run as direct transfers.  A request of at least half a transparent huge page
+ * is mapped at a huge-page boundary, rounded up to whole huge pages, and the
+ * kernel is asked for huge pages (advice: small pages where it has none); a
+ * smaller one, or any request where transparent huge pages are off, uses the
+ * system page size.  *out receives the start (aligned to the huge page or page
+ * size it was mapped with); the caller owns the buffer until
  * lbm_host_free.  Returns LBM_ERR_INVALID_ARG for bytes == 0 or out == NULL,
  * LBM_ERR_OOM if the mapping fails, LBM_ERR_CUDA if the registration fails (no
  * CUDA device, for one); *out is NULL on any error.  Not synchronising; costs

@@ -4,12 +4,12 @@
 // On a Grace host the GPU reads and writes host memory over NVLink-C2C, and a
 // buffer made of small pages can copy several times slower than the link allows
 // when the GPU touches it for the first time in a while: what the copy engines
-// pay is address translation, not bandwidth.  These buffers are mapped on a
-// transparent-huge-page boundary, sized in whole huge pages and advised for huge
-// pages before their first touch, so that a few large pages cover a field of
-// ~0.5 GB; they are then registered (page-locked) with the CUDA runtime.  Where
-// the kernel gives no huge pages the buffer is still page-locked, with the
-// system's page size.
+// pay is address translation, not bandwidth.  Buffers of at least half a
+// transparent huge page are mapped on a huge-page boundary, sized in whole huge
+// pages and advised for huge pages before their first touch, so that a few large
+// pages cover a field of ~0.5 GB; smaller ones use the system's pages.  Both are
+// then registered (page-locked) with the CUDA runtime.  Where the kernel gives no
+// huge pages the buffer is still page-locked, with the system's page size.
 #include <cuda_runtime.h>
 #include <sys/mman.h>
 #include <unistd.h>
@@ -59,7 +59,9 @@ extern "C" lbm_status lbm_host_alloc(size_t bytes, void** out) {
   const long sys_page = sysconf(_SC_PAGESIZE);
   const size_t page = sys_page > 0 ? (size_t)sys_page : 4096;
   const size_t huge = huge_page_bytes();
-  const size_t unit = huge > page && huge % page == 0 ? huge : page;
+  // huge pages for buffers of at least half a huge page (512 MB pages on a 64 KB-page
+  // Arm kernel would waste most of their memory on small buffers); pages otherwise
+  const size_t unit = huge > page && huge % page == 0 && bytes >= huge / 2 ? huge : page;
   if (bytes > SIZE_MAX - 2 * unit) return LBM_ERR_INVALID_ARG;
   const size_t length = (bytes + unit - 1) / unit * unit;
   // map one unit more than needed, keep the aligned part, return the rest
