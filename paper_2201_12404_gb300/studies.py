@@ -407,6 +407,44 @@ def paper_2d_impacts(R0=100.0, sigma=SIGMA_T059, cases=PAPER_2D_CASES):
     return out
 
 
+# The paper's 3-D impacts (Sec. 3.3): We 82, 167 and 328 for one fluid (water/air), so
+# Re grows as sqrt(We) over the stated 3500-6900; R0 = 80 in a 14 R0 x 14 R0 x 6 R0 box,
+# a film h/2R0 = 0.22, 5% white noise on the drop's velocity, T/Tc = 0.59, nu_v = 15 nu_l.
+PAPER_3D_WE = (82, 167, 328)
+PAPER_3D_RE_AT_FIRST = 3500.0
+
+
+def paper_3d_impacts(R0=80.0, sigma=SIGMA_T059, weber=PAPER_3D_WE, re_first=PAPER_3D_RE_AT_FIRST):
+    """Workloads of the paper's 3-D impact cases at the paper's EOS and kappa: U0 from
+    We and sigma, one liquid viscosity for all (Re = re_first at the first We)."""
+    T = 0.59
+    rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=T, **WL.PAPER_EOS))
+    U = [math.sqrt(We * sigma / (2.0 * rl * R0)) for We in weber]
+    nu = 2.0 * U[0] * R0 / re_first
+    out = []
+    for We, u in zip(weber, U):
+        Re = 2.0 * u * R0 / nu
+        n, nz = int(14 * R0), int(6 * R0)
+        out.append(WL.Workload(name=f"paper 3-D impact We={We} Re={Re:.0f} ({n}x{n}x{nz}, R0={R0:g})",
+                               D=3, nx=n, ny=n, nz=nz, T_over_Tc=T, kappa=0.01, nu_liquid=nu, mu_ratio=0.0,
+                               R=R0, U=u, film=0.44, walls_axis=2, noise=0.05,
+                               extra={"nu_vapour_ratio": 15.0, "We": We, "Re": Re}))
+    return out
+
+
+def paper_3d_crown_study(quick=False, t_end_tau=1.0):
+    """Crown radius series of the paper's three 3-D impact cases at the paper's size
+    (6.0e8 nodes, 85 GB each; about a minute per convective time on one GB300); quick
+    runs them at R0 = 20.  A case that diverges is reported with the step it reached."""
+    rows = []
+    for wl in paper_3d_impacts(R0=20.0 if quick else 80.0):
+        res = crown_study(wl=wl, t_end_tau=t_end_tau, samples=40)
+        rows.append(dict(We=wl.extra["We"], Re=wl.extra["Re"], U0=wl.U, nu_l=wl.nu_liquid,
+                         **{k: res[k] for k in ("tau", "t", "r", "t_contact", "fit", "failed", "seconds", "mlups",
+                                                "interface_width") if k in res}))
+    return dict(cases=rows)
+
+
 def paper_crown_study(quick=False, t_end_tau=2.0):
     """Crown radius series of the paper's four 2-D impact cases and their exponents.
     The cases run at the paper's resolution (R0 = 100: under a second each on one
@@ -517,13 +555,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["spurious", "stability", "surface-tension", "crown", "coexistence"])
     ap.add_argument("--quick", action="store_true", help="small sizes and few steps")
-    ap.add_argument("--workload", default=None, help="crown: a workload name (default drop2d; drop3d-paper: the paper's 3-D size; paper-2d: the paper's four 2-D cases)")
+    ap.add_argument("--workload", default=None, help="crown: a workload name (default drop2d; drop3d-paper: the paper's 3-D size at We ~ 20; paper-2d: the paper's four 2-D cases; paper-3d: the paper's three 3-D cases)")
     ap.add_argument("--tau", type=float, default=2.0, help="crown: simulated time in convective times 2R/U")
     ap.add_argument("--a", default=None, help="surface-tension: comma-separated EOS constants a (default 0.003,0.0017,0.0011)")
     args = ap.parse_args()
     lbm.load()
     if args.study == "crown" and args.workload == "paper-2d":
         res = paper_crown_study(args.quick, t_end_tau=args.tau)
+    elif args.study == "crown" and args.workload == "paper-3d":
+        res = paper_3d_crown_study(args.quick, t_end_tau=args.tau)
     elif args.study == "crown":
         res = crown_study(args.quick, wl=WL.by_name(args.workload) if args.workload else None, t_end_tau=args.tau)
     elif args.study == "coexistence":

@@ -53,7 +53,8 @@ class Workload:
 # We = 2 rho_l R U^2 / sigma with rho_l = 8.78, and Re = 2 U R / nu_l.  A Weber
 # number near 250 at these R and U would need sigma 8 times smaller, which lowering
 # a and kappa gives only with a vapour sound speed below half the impact speed, and
-# such impacts diverge at contact.
+# such impacts diverge at contact.  The paper's 3-D Weber numbers are reached through
+# the impact speed instead (studies.paper_3d_impacts).
 SIGMA_T059 = 0.175
 
 # D3Q27 drop impact on a thin film, 512x512x256, density ratio ~1000 (T/Tc = 0.59)

@@ -107,6 +107,29 @@ def test_paper_2d_impacts_reproduce_the_stated_we_and_re():
         assert nu_v == 15 * nu_l
 
 
+def test_paper_3d_impacts_reproduce_the_stated_we_and_re_range():
+    """Sec. 3.3: We 82, 167 and 328 in a 14 R0 x 14 R0 x 6 R0 box with R0 = 80 and
+    h/2R0 = 0.22, one fluid for all three, so that Re grows as sqrt(We) and spans the
+    stated 3500-6900 (to the rounding of the paper's figures); nu_v = 15 nu_l."""
+    import math
+    from paper_2201_12404_gb300 import lbm
+    from paper_2201_12404_gb300 import workloads as WL
+    rv, rl, _ = lbm.lbm_coexistence(lbm.lbm_default_params(T_over_Tc=0.59, **WL.PAPER_EOS))
+    wls = S.paper_3d_impacts()
+    assert [w.extra["We"] for w in wls] == [82, 167, 328]
+    for w in wls:
+        assert (w.nx, w.ny, w.nz, w.R, w.walls_axis) == (1120, 1120, 480, 80.0, 2)
+        assert abs(w.film * w.R / (2 * w.R) - 0.22) < 1e-12 and w.noise == 0.05
+        assert abs(2 * rl * w.R * w.U ** 2 / S.SIGMA_T059 - w.extra["We"]) < 1e-9 * w.extra["We"]
+        assert abs(2 * w.U * w.R / w.nu_liquid - w.extra["Re"]) < 1e-9 * w.extra["Re"]
+        assert w.nu_liquid == wls[0].nu_liquid
+        nu_l, nu_v = WL.viscosities(w, rv, rl)
+        assert nu_v == 15 * nu_l
+    res = [w.extra["Re"] for w in wls]
+    assert abs(res[0] - 3500) < 1e-6 and 6800 < res[-1] < 7100
+    assert abs(res[-1] / res[0] - math.sqrt(328 / 82)) < 1e-9
+
+
 def test_surface_tension_study_scales_radii_and_steps_with_a(monkeypatch):
     """Without a GPU: the study asks for drops whose radii grow as sqrt(a0/a) (the
     interface width at fixed kappa) and run a0/a times longer, for each a."""
