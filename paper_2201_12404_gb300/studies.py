@@ -435,7 +435,9 @@ def paper_3d_impacts(R0=80.0, sigma=SIGMA_T059, weber=PAPER_3D_WE, re_first=PAPE
 def paper_3d_crown_study(quick=False, t_end_tau=1.0):
     """Crown radius series of the paper's three 3-D impact cases at the paper's size
     (6.0e8 nodes, 85 GB each; about a minute per convective time on one GB300); quick
-    runs them at R0 = 20.  A case that diverges is reported with the step it reached."""
+    runs them at R0 = 20, where the same We needs twice the impact speed (and the
+    faster cases diverge sooner).  A case that diverges is reported with the step it
+    reached."""
     rows = []
     for wl in paper_3d_impacts(R0=20.0 if quick else 80.0):
         res = crown_study(wl=wl, t_end_tau=t_end_tau, samples=40)
