@@ -360,6 +360,8 @@ def crown_study(quick=False, wl=None, t_end_tau=2.0, samples=100, precision=lbm.
                 out["r"].append(dom.lbm_crown_radius(layer))
         except lbm.LBMError as e:
             out["failed"] = dict(after_step=done, within=every, error=str(e)[:120])
+            hit = [t for t, r in zip(out["t"], out["r"]) if r > 0]
+            out["t_contact"] = hit[0] if hit else None  # the crown had formed before the failure
             return out
         out["seconds"] = time.perf_counter() - t0
         out["mlups"] = wl.N * n_end / out["seconds"] / 1e6
