@@ -162,3 +162,40 @@ def test_crown_fits_recover_the_exponent_of_each_window():
     assert [f["window_tau"] for f in fits] == [[0.01, 0.1], [0.2, 1.0]]
     assert abs(fits[0]["p"] - 0.5) < 1e-9 and abs(fits[0]["c"] - 3.0) < 1e-9
     assert abs(fits[1]["p"] - 0.9) < 1e-9
+
+
+def test_crown_study_reports_contact_and_failure_of_a_run_that_diverges(monkeypatch):
+    """Without a GPU (a fake domain): a run whose crown forms and that then diverges
+    reports the step it reached and the contact step of its crown."""
+    import dataclasses
+    from paper_2201_12404_gb300 import workloads as WL
+
+    class FakeDomain:
+        def __init__(self, p):
+            self.steps = 0
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            return False
+
+        def lbm_init_drop_on_film(self, *a, **k):
+            pass
+
+        def lbm_record_gamma(self, on):
+            pass
+
+        def lbm_step(self, n):
+            if self.steps + n > 60:
+                raise lbm.LBMError(lbm.LBM_ERR_UNSTABLE, "non-finite density")
+            self.steps += n
+
+        def lbm_crown_radius(self, layer):
+            return 0.0 if self.steps < 30 else float(self.steps)
+
+    monkeypatch.setattr(S.lbm, "Domain", FakeDomain)
+    wl = dataclasses.replace(WL.DROP_IMPACT_2D, R=10.0, U=0.1)  # tau = 200 steps
+    res = S.crown_study(wl=wl, t_end_tau=1.0, samples=20)      # samples every 10 steps
+    assert res["failed"]["after_step"] == 60 and res["t_contact"] == 30
+    assert res["t"] == [10, 20, 30, 40, 50, 60]
